@@ -1,0 +1,311 @@
+"""Pins of the FP64 oracle against things other than itself: a dense reconstruction by
+mode products, special cases that reduce to matrix algebra, symbolic differentiation,
+central finite differences, algebraic identities between its routes, and recovery of a
+planted model to its noise floor.  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.oracle_cases import Cpl, Prob, dense_tucker, random_problem
+
+
+def make(prob, params, **hp):
+    o = oracle.Oracle(prob, **hp)
+    o.set_params(*params)
+    return o
+
+
+# ------------------------------------------------------------------ Eq. (4): prediction
+@pytest.mark.parametrize("dims,J", [((7, 6, 5), (2, 3, 4)), ((5, 4, 3, 3), (2, 2, 3, 2))])
+def test_predict_equals_dense_reconstruction(dims, J):
+    prob, params = random_problem(dims, J, nnz=20, seed=1)
+    o = make(prob, params)
+    G, U, _ = params
+    X = dense_tucker(G, U)                      # Tucker model of Section 2.2, matrix form
+    cells = np.stack(np.unravel_index(np.arange(X.size), dims)).astype(np.int32)
+    np.testing.assert_allclose(o.predict(cells), X.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_predict_cfg0_all_cells():
+    """Brute force over all 200k cells of a 100x100x20 tensor with a 5x5x5 core."""
+    prob, params = random_problem((100, 100, 20), (5, 5, 5), nnz=50, seed=2)
+    o = make(prob, params)
+    X = dense_tucker(params[0], params[1])
+    cells = np.stack(np.unravel_index(np.arange(X.size), X.shape)).astype(np.int32)
+    np.testing.assert_allclose(o.predict(cells), X.ravel(), rtol=1e-12, atol=1e-12)
+
+
+def test_predict_order2_is_bilinear_form():
+    rng = np.random.default_rng(3)
+    dims, J = (9, 8), (3, 4)
+    idx = np.stack(np.unravel_index(np.arange(72), dims)).astype(np.int32)
+    prob = Prob(dims, J, idx, np.zeros(72), [])
+    G = rng.normal(size=J)
+    U = [rng.random((9, 3)), rng.random((8, 4))]
+    o = make(prob, (G, U, []))
+    expect = U[0] @ G @ U[1].T                 # x~_{i1 i2} = u1^T G u2
+    np.testing.assert_allclose(o.predict(idx), expect.ravel(), rtol=1e-12)
+
+
+def test_predict_hyperdiagonal_core_is_cp():
+    """Section 2.2: a hyper-diagonal core with equal ranks gives the CP model."""
+    rng = np.random.default_rng(4)
+    dims, R = (6, 5, 4), 3
+    G = np.zeros((R, R, R))
+    lam = rng.normal(size=R)
+    for r in range(R):
+        G[r, r, r] = lam[r]
+    U = [rng.random((d, R)) for d in dims]
+    idx = np.stack(np.unravel_index(np.arange(120), dims)).astype(np.int32)
+    o = make(Prob(dims, (R,) * 3, idx, np.zeros(120), []), (G, U, []))
+    cp = np.einsum("r,ir,jr,kr->ijk", lam, *U)
+    np.testing.assert_allclose(o.predict(idx), cp.ravel(), rtol=1e-12)
+
+
+# ------------------------------------------------------------------ Eq. (3): partial products
+def test_partials_are_derivatives_of_prediction():
+    """G x_{-n} {u} is the derivative of the (multilinear) prediction w.r.t. row n, and
+    its dot product with row n gives the prediction back."""
+    prob, params = random_problem((5, 4, 3, 3), (2, 3, 2, 3), nnz=10, seed=5)
+    o = make(prob, params)
+    alpha = np.array([1, 2, 0, 2], dtype=np.int32)
+    parts = o.partials(alpha)
+    xt = o.predict(alpha.reshape(4, 1))[0]
+    G, U, V = params
+    for n in range(4):
+        assert np.dot(parts[n], U[n][alpha[n]]) == pytest.approx(xt, rel=1e-12)
+        for k in range(prob.J[n]):
+            Up = [u.copy() for u in U]
+            Um = [u.copy() for u in U]
+            h = 1e-4
+            Up[n][alpha[n], k] += h
+            Um[n][alpha[n], k] -= h
+            o.set_params(G, Up, V)
+            fp = o.predict(alpha.reshape(4, 1))[0]
+            o.set_params(G, Um, V)
+            fm = o.predict(alpha.reshape(4, 1))[0]
+            assert (fp - fm) / (2 * h) == pytest.approx(parts[n][k], rel=1e-9, abs=1e-12)
+        o.set_params(G, U, V)
+
+
+# ------------------------------------------------------------------ Eq. (7): the objective
+def test_loss_forms_agree_and_match_numpy():
+    prob, params = random_problem((8, 7, 6), (3, 2, 4), nnz=60, seed=6)
+    hp = dict(lambda_reg=0.3, lambda_m=2.5)
+    o = make(prob, params, **hp)
+    f, se, sy = o.loss()
+    assert o.loss_rowform() == pytest.approx(f, rel=1e-12)
+    # the same number from a dense reconstruction and plain norms
+    G, U, V = params
+    X = dense_tucker(G, U)
+    pred = X[tuple(prob.train_idx)]
+    se_np = np.sum((prob.train_val - pred) ** 2)
+    assert se == pytest.approx(se_np, rel=1e-12)
+    reg = np.sum(G ** 2)
+    for n in range(3):
+        touched = np.unique(prob.train_idx[n])
+        reg += np.sum(U[n][touched] ** 2)
+    c = prob.coupled[0]
+    e_y = c.vals - np.sum(U[c.mode][c.rows] * V[0][c.cols], axis=1)
+    rv = np.sum(V[0][np.unique(c.cols)] ** 2)
+    f_np = 0.5 * se_np + 0.5 * hp["lambda_reg"] * reg + 0.5 * hp["lambda_m"] * (
+        np.sum(e_y ** 2) + hp["lambda_reg"] * rv)
+    assert f == pytest.approx(f_np, rel=1e-12)
+    assert sy[0] == pytest.approx(np.sum(e_y ** 2), rel=1e-12)
+
+
+def test_rmse_definition():
+    prob, params = random_problem((6, 6, 6), (2, 2, 2), nnz=30, seed=7)
+    o = make(prob, params)
+    X = dense_tucker(params[0], params[1])
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, 6, size=(3, 40)).astype(np.int32)
+    val = rng.normal(size=40)
+    expect = np.sqrt(np.mean((val - X[tuple(idx)]) ** 2))
+    assert o.rmse(idx, val) == pytest.approx(expect, rel=1e-12)
+
+
+# ------------------------------------------------------------------ Eq. (8): gradients
+@pytest.mark.parametrize("dims,J,ncpl", [((6, 5, 4), (2, 3, 2), 1), ((5, 4, 3, 3), (2, 2, 3, 2), 2),
+                                        ((7, 5, 4), (3, 3, 3), 0)])
+def test_full_gradient_central_differences(dims, J, ncpl):
+    prob, params = random_problem(dims, J, nnz=35, n_coupled=ncpl, seed=8, coupled_nnz=15)
+    hp = dict(lambda_reg=0.2, lambda_m=1.7)
+    o = make(prob, params, **hp)
+    gG, gU, gV = o.full_gradient()
+    G, U, V = params
+    rng = np.random.default_rng(1)
+
+    def f_at(G_, U_, V_):
+        o.set_params(G_, U_, V_)
+        return o.loss()[0]
+
+    checks = []
+    for l in rng.choice(G.size, size=min(G.size, 10), replace=False):
+        checks.append(("G", None, np.unravel_index(l, G.shape)))
+    for n in range(len(dims)):
+        for _ in range(6):
+            checks.append(("U", n, (rng.integers(dims[n]), rng.integers(J[n]))))
+    for m in range(ncpl):
+        for _ in range(6):
+            checks.append(("V", m, (rng.integers(V[m].shape[0]), rng.integers(V[m].shape[1]))))
+    for kind, k, pos in checks:
+        Gp, Up, Vp = G.copy(), [u.copy() for u in U], [v.copy() for v in V]
+        Gm, Um, Vm = G.copy(), [u.copy() for u in U], [v.copy() for v in V]
+        tgt_p = Gp if kind == "G" else (Up[k] if kind == "U" else Vp[k])
+        tgt_m = Gm if kind == "G" else (Um[k] if kind == "U" else Vm[k])
+        x = tgt_p[pos]
+        h = 1e-6 * max(1.0, abs(x))
+        tgt_p[pos] += h
+        tgt_m[pos] -= h
+        fd = (f_at(Gp, Up, Vp) - f_at(Gm, Um, Vm)) / (2 * h)
+        an = gG[pos] if kind == "G" else (gU[k][pos] if kind == "U" else gV[k][pos])
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-7), (kind, k, pos)
+
+
+def test_untouched_rows_have_zero_gradient():
+    prob, params = random_problem((10, 4, 4), (2, 2, 2), nnz=6, n_coupled=0, seed=9)
+    o = make(prob, params, lambda_reg=0.5)
+    _, gU, _ = o.full_gradient()
+    untouched = np.setdiff1d(np.arange(10), prob.train_idx[0])
+    assert untouched.size > 0
+    assert np.all(gU[0][untouched] == 0.0)
+
+
+def test_entry_gradients_sum_to_full_gradient():
+    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=25, n_coupled=0, seed=10)
+    o = make(prob, params, lambda_reg=0.4)
+    gG, gU, _ = o.full_gradient()
+    sG = np.zeros_like(gG)
+    sU = [np.zeros_like(u) for u in gU]
+    for e in range(25):
+        _, gu, g = o.entry_gradient(e)
+        sG += g
+        for n in range(3):
+            sU[n][prob.train_idx[n][e]] += gu[n]
+    np.testing.assert_allclose(sG, gG, rtol=1e-12, atol=1e-12)
+    for n in range(3):
+        np.testing.assert_allclose(sU[n], gU[n], rtol=1e-12, atol=1e-12)
+
+
+def test_opt_route_equals_naive_route():
+    """Lemma 2 / Lemma 3 (Section 3.5): S, Collapse and element-wise division give the
+    same per-entry gradients as Eq. (8) on inputs without zeros."""
+    prob, params = random_problem((6, 5, 4, 3), (2, 3, 2, 2), nnz=12, n_coupled=0, seed=11,
+                                  zero_free=True)
+    o = make(prob, params, lambda_reg=0.3)
+    for e in range(12):
+        e1, gu1, gG1 = o.entry_gradient(e)
+        e2, gu2, gG2 = o.entry_gradient_opt(e)
+        assert e1 == pytest.approx(e2, rel=1e-12)
+        for a, b in zip(gu1, gu2):
+            np.testing.assert_allclose(a, b, rtol=1e-10, atol=1e-12)
+        np.testing.assert_allclose(gG1, gG2, rtol=1e-10, atol=1e-12)
+
+
+def test_rank_one_sgd_step_by_symbolic_differentiation():
+    """J = 1: one sequential step over a tensor entry then a coupled entry, with the
+    gradients obtained by sympy from the scalar per-entry objective."""
+    sympy = pytest.importorskip("sympy")
+    g, a, b, c, w = sympy.symbols("g a b c w")
+    x, y, lam, lm, eta = 3.1, -0.7, 0.3, 2.0, 0.05
+    vals = {g: 0.9, a: 0.4, b: -1.3, c: 0.8, w: 0.6}
+    # per-entry terms of f (Eq. (7)); |Omega| = 1 and every count is 1
+    f_alpha = sympy.Rational(1, 2) * ((x - g * a * b * c) ** 2 + lam * g ** 2 + lam * (a ** 2 + b ** 2 + c ** 2))
+    f_beta = lm / 2 * ((y - a * w) ** 2 + lam * w ** 2)
+    step1 = {s: float(vals[s] - eta * sympy.diff(f_alpha, s).subs(vals)) for s in (g, a, b, c)}
+    step1[w] = vals[w]
+    step2 = dict(step1)
+    for s in (a, w):
+        step2[s] = float(step1[s] - eta * sympy.diff(f_beta, s).subs(step1))
+    idx = np.zeros((3, 1), dtype=np.int32)
+    prob = Prob((1, 1, 1), (1, 1, 1), idx, np.array([x]),
+                [Cpl(0, 1, np.zeros(1, np.int32), np.zeros(1, np.int32), np.array([y]))])
+    o = make(prob, (np.array([[[0.9]]]), [np.array([[0.4]]), np.array([[-1.3]]), np.array([[0.8]])],
+                    [np.array([[0.6]])]), lambda_reg=lam, lambda_m=lm, lr0=eta, mu=0.0)
+    o.epoch_sequential(0, np.array([0, 1]))
+    G, U, V = o.get_params()
+    assert G.ravel()[0] == pytest.approx(step2[g], rel=1e-13)
+    assert U[0][0, 0] == pytest.approx(step2[a], rel=1e-13)
+    assert U[1][0, 0] == pytest.approx(step2[b], rel=1e-13)
+    assert U[2][0, 0] == pytest.approx(step2[c], rel=1e-13)
+    assert V[0][0, 0] == pytest.approx(step2[w], rel=1e-13)
+
+
+# ------------------------------------------------------------------ Alg. 1 and the minibatch rule
+def test_learning_rate_schedule():
+    prob, params = random_problem((3, 3, 3), (1, 1, 1), nnz=3, n_coupled=0)
+    o = make(prob, params, lr0=0.02, mu=0.1)
+    assert o.learning_rate(0) == pytest.approx(0.02)
+    assert o.learning_rate(5) == pytest.approx(0.02 / 1.5)
+
+
+def test_minibatch_of_one_is_sequential():
+    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=12,
+                                  coupled_nnz=20)
+    order = np.random.default_rng(0).permutation(60)
+    a = make(prob, params, lr0=0.05, mu=0.1, lambda_reg=0.2, lambda_m=1.5)
+    b = make(prob, params, lr0=0.05, mu=0.1, lambda_reg=0.2, lambda_m=1.5, batch=1)
+    for t in range(2):
+        a.epoch_sequential(t, order)
+        b.epoch_minibatch(t, order)
+    for x, y in zip([a.G] + a.U + a.V, [b.G] + b.U + b.V):
+        np.testing.assert_allclose(x, y, rtol=1e-13, atol=1e-14)
+
+
+def test_full_batch_is_a_gradient_step():
+    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=13,
+                                  coupled_nnz=20)
+    hp = dict(lr0=0.03, mu=0.0, lambda_reg=0.2, lambda_m=1.5, core_scale=2.0)
+    o = make(prob, params, **hp)
+    gG, gU, gV = o.full_gradient()
+    o.epoch_minibatch(0, np.arange(60), batch=60)
+    G, U, V = params
+    np.testing.assert_allclose(o.G, G - 0.03 * 2.0 * gG / 40, rtol=1e-12, atol=1e-14)
+    for n in range(3):
+        np.testing.assert_allclose(o.U[n], U[n] - 0.03 * gU[n], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(o.V[0], V[0] - 0.03 * gV[0], rtol=1e-12, atol=1e-14)
+
+
+def test_minibatch_mean_rule_divides_by_row_hits():
+    prob, params = random_problem((3, 3, 3), (2, 2, 2), nnz=12, n_coupled=0, seed=14)
+    o = make(prob, params, lr0=0.03, mu=0.0, lambda_reg=0.1)
+    _, gU, _ = o.full_gradient()
+    o.epoch_minibatch(0, np.arange(12), batch=12, row_mean=1)
+    hits = np.bincount(prob.train_idx[0], minlength=3)
+    U0 = params[1][0]
+    expect = U0 - 0.03 * gU[0] / np.maximum(hits, 1)[:, None]
+    np.testing.assert_allclose(o.U[0], expect, rtol=1e-12, atol=1e-14)
+
+
+def test_order_outside_union_is_rejected():
+    prob, params = random_problem((3, 3, 3), (1, 1, 1), nnz=3, n_coupled=0)
+    o = make(prob, params)
+    with pytest.raises(ValueError):
+        o.epoch_sequential(0, np.array([0, 1, 7]))
+
+
+# ------------------------------------------------------------------ planted recovery
+def test_recovers_planted_model_to_noise_floor():
+    from paper_1708_08640_gb300 import synth
+    p = synth.make_problem("cfg0")                   # noise sigma = 0.1
+    o = oracle.Oracle(p, lr0=0.02, mu=0.0, lambda_reg=0.01, lambda_m=1.0)
+    o.set_params(*synth.init_params(p, 1))
+    order = synth.union_order(p, 2)
+    for t in range(40):
+        o.epoch_sequential(t, order)
+    assert o.rmse(p.test_idx, p.test_val) <= 1.3 * 0.1
+
+
+def test_noiseless_planted_model_train_error_goes_to_zero():
+    from paper_1708_08640_gb300 import synth
+    p = synth.make_problem("cfg0", noise=0.0)
+    o = oracle.Oracle(p, lr0=0.02, mu=0.0, lambda_reg=0.0, lambda_m=1.0)
+    o.set_params(*synth.init_params(p, 1))
+    order = synth.union_order(p, 2)
+    hist = []
+    for t in range(50):
+        o.epoch_sequential(t, order)
+        hist.append(o.rmse(p.train_idx, p.train_val))
+    assert np.all(np.diff(hist[15:]) < 0)
+    assert hist[-1] < 0.01
