@@ -1,0 +1,361 @@
+#!/usr/bin/env python3
+"""Epoch throughput of the S3CMTF GB300 path (SGD nnz-updates/s) on synthetic data shaped
+like the paper's rating-tensor workloads.
+
+One step = one SGD epoch over every observed item (train tensor entries and coupled-matrix
+entries) followed by the test-RMSE pass; value = items updated per second over the K timed
+steps (CUDA events on the library's stream, barrier + synchronize on both sides, max over
+ranks).  The gradient pass (differentiation form) and the deterministic minibatch epoch are
+timed in the same run and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload cfg1] [--mode hogwild|minibatch]
+
+N > 1 runs N independent replicas (one per rank, one problem each; weak scaling) -- the
+method has no data-path exchange to distribute.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1708_08640_gb300 import synth  # noqa: E402
+
+METRIC = "SGD nnz-updates/s at matched test RMSE, BF16 vs FP32 form; gradient-pass GB/s"
+UNIT = "nnz-updates/s"
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# FP32 FFMA roof of the CUDA-core form: SMs x FP32 lanes x 2 flop x max SM clock
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+KERNEL_SOURCES = ["paper_1708_08640_gb300/csrc/k_tensor.cu",
+                  "paper_1708_08640_gb300/csrc/tensor_fp32.cuh",
+                  "paper_1708_08640_gb300/csrc/common.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="cfg1")
+    ap.add_argument("--mode", choices=["hogwild", "minibatch"], default="hogwild")
+    ap.add_argument("--cpu-sample", type=int, default=600_000,
+                    help="items of the visiting order the CPU oracle baseline processes")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the gradient-pass and minibatch side measurements")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def source_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def committed_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = source_sha()
+    for line in open(path):
+        f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if f.get("kernel") == kernel and f.get("workload") == workload and f.get("sha") == sha:
+            return float(f["bytes_per_launch"])
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def cpu_baseline(p, sample, order):
+    """The FP64 oracle (as it stands: one thread, plain loops) on a bounded prefix of the
+    visiting order: sequential SGD (Algorithm 1, P = 1)."""
+    import oracle
+    o = oracle.Oracle(p, **{k: v for k, v in p.hparams.items()
+                           if k in ("lr0", "mu", "lambda_reg", "lambda_m", "batch", "core_scale")})
+    o.set_params(*synth.init_params(p, 1))
+    sub = order[:sample]
+    t0 = time.perf_counter()
+    o.epoch_sequential(0, sub)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {sample} items of the {p.name} visiting order, one sequential "
+                      f"SGD pass (Algorithm 1, P=1), FP64, {dt:.1f} s"}
+
+
+def workload_desc(p, mode, precision="fp32"):
+    return {"workload": f"{p.name}: {p.recipe}; J={p.J}; {precision.upper()} form, {mode}",
+            "dims": list(p.dims), "J": list(p.J), "train_nnz": p.nnz,
+            "coupled_nnz": [c.nnz for c in p.coupled], "test_nnz": int(p.test_val.shape[0]),
+            "hparams": p.hparams, "mode": mode, "precision": precision,
+            "l2": "inputs larger than L2 (COO and layout arrays >> 129 MB); no flush"}
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle  # noqa: F401
+    p = synth.make_problem(args.workload)
+    order = synth.union_order(p, 2)
+    o = oracle.Oracle(p, **{k: v for k, v in p.hparams.items()
+                           if k in ("lr0", "mu", "lambda_reg", "lambda_m", "batch", "core_scale")})
+    o.set_params(*synth.init_params(p, 1))
+    S = max(1000, min(args.cpu_sample // 4, p.n_union))
+    for w in range(args.warmup):
+        o.epoch_sequential(0, order[(w * S) % p.n_union:][:S])
+    times = []
+    for k in range(args.steps):
+        s0 = ((args.warmup + k) * S) % p.n_union
+        t0 = time.perf_counter()
+        o.epoch_sequential(0, order[s0:s0 + S])
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = S / (ms / 1000.0)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(workload_desc(p, "sequential", "fp64"),
+                           step=f"{S} items of the visiting order per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{S} items per step, sequential Algorithm 1, FP64"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, world, rank, local):
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1708_08640_gb300 import _lib as L
+    from paper_1708_08640_gb300.model import S3CMTF
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # each rank fits its own replica problem (weak scaling)
+    p = synth.make_problem(args.workload, seed=rank)
+    order = synth.union_order(p, 2)
+    stream = torch.cuda.Stream()
+    model = S3CMTF.from_problem(p, order=order, stream=stream)
+    model.set_params(*synth.init_params(p, 1))
+    model.set_test(p.test_idx, p.test_val)
+    lib, ctx = model.lib, model.ctx
+
+    def step():
+        model.epoch(args.mode, "fp32")
+        return model.rmse()
+
+    rmse0 = model.rmse()
+    for _ in range(args.warmup):
+        step()
+    # ---- timed region
+    L.check(lib, ctx, lib.s3_profile(ctx, 1))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    rmses = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    items = p.n_union
+    value = world * items * args.steps / (ms_total / 1000.0)
+
+    def read(fam):
+        ms, n, e = C.c_double(), C.c_int64(), C.c_int64()
+        L.check(lib, ctx, lib.s3_profile_read(ctx, fam, C.byref(ms), C.byref(n), C.byref(e)))
+        return ms.value, n.value, e.value
+
+    fam = L.S3_K_TENSOR_HOG if args.mode == "hogwild" else L.S3_K_TENSOR_MB
+    k_ms, k_n, k_entries = read(fam)
+    _, launches, _ = read(L.S3_K_ALL)
+    L.check(lib, ctx, lib.s3_profile(ctx, 0))
+    J = p.J
+    flops_per_entry = 6.0 * float(np.prod(J)) if p.N == 3 else (
+        6.0 * float(np.prod(J)) + 4.0 * float(np.prod(J[:3])))
+    achieved = flops_per_entry * k_entries / (k_ms / 1000.0) / 1e12 if k_ms > 0 else None
+    kname = "k_tensor_hog" if args.mode == "hogwild" else "k_tensor_contrib"
+    traffic = committed_traffic(kname, args.workload)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
+                "traffic": traffic, "kernel": kname, "launches": k_n,
+                "kernel_ms_per_step": k_ms / args.steps,
+                "flops_per_entry": flops_per_entry,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+
+    extras = {}
+    if not args.no_extras:
+        # gradient pass (differentiation form): bytes moved per pass / time
+        model.gradient()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ng = 3
+        for _ in range(ng):
+            model.gradient()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        g_ms = e0.elapsed_time(e1) / ng
+        coo = p.nnz * (4 * p.N + 4) + sum(c.nnz * 12 for c in p.coupled)
+        rows = sum(int(np.unique(p.train_idx[n]).shape[0]) * J[n] for n in range(p.N))
+        rows += sum(int(np.unique(c.cols).shape[0]) * J[c.mode] for c in p.coupled)
+        grad_out = int(np.prod(J)) + sum(d * j for d, j in zip(p.dims, J)) + sum(
+            c.K * J[c.mode] for c in p.coupled)
+        gbytes = coo + 4 * rows + 4 * grad_out
+        extras["gradient_pass"] = {"ms": g_ms, "GB/s": gbytes / (g_ms / 1000.0) / 1e9,
+                                   "bytes": gbytes}
+        if args.mode != "minibatch":
+            m2 = S3CMTF.from_problem(p, order=order, stream=stream)
+            m2.set_params(*synth.init_params(p, 1))
+            m2.epoch("minibatch")
+            torch.cuda.synchronize()
+            e0.record(stream)
+            m2.epoch("minibatch")
+            e1.record(stream)
+            torch.cuda.synchronize()
+            mb_ms = e0.elapsed_time(e1)
+            extras["minibatch_epoch"] = {"ms": mb_ms, "nnz_updates_per_s": items / (mb_ms / 1000.0),
+                                         "batches": model.info()["n_batches"]}
+            m2.close()
+
+    # ---- end to end through the public API with host buffers
+    xv = torch.tensor(p.train_val, dtype=torch.float32).pin_memory()
+    yv = [torch.tensor(c.vals, dtype=torch.float32).pin_memory() for c in p.coupled]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        model.update_values(xv, yv)
+        model.epoch(args.mode, "fp32")
+        model.rmse()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    h2d = 4 * items + 4
+    e2e = {"value": world * items * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12}
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline(p, min(args.cpu_sample, p.n_union), order)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_desc(p, args.mode), parallelism=f"replicas x{world}"),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk,
+                "test_rmse": {"before": rmse0, "per_step": rmses}, **extras}
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * s3cmtf.h -- C ABI of the GB300 (sm_103a) implementation of the S3CMTF hot path:
+ * the per-nonzero SGD epoch of sparse coupled Tucker matrix-tensor factorisation
+ * (Choi, Jang, Kang: "Fast, Accurate, and Scalable Method for Sparse Coupled
+ * Matrix-Tensor Factorization", Section 3).
+ *
+ * Model (Section 2.2, Eq. (4); Section 2.3, Definition 1):
+ *   x~_alpha = G x {u}_alpha = sum_j g_j prod_n u^(n)_{i_n j_n}        (tensor entry)
+ *   y~_beta  = u^(c)_{j1} . v_{j2}                                      (coupled entry)
+ * Objective (Eq. (7) and the per-entry sums after it):
+ *   f = 1/2 sum_alpha [ e_alpha^2 + lambda_reg/|Omega| ||G||^2
+ *                       + lambda_reg sum_n ||u^(n)_{i_n}||^2 / |Omega^{n,i_n}| ]
+ *     + sum_m lambda_m/2 sum_beta [ e_beta^2 + lambda_reg/|Omega_Y^{2,j2}| ||v_{j2}||^2 ]
+ * Per-entry gradients: Eq. (8).  Epoch: Algorithm 1 (with compute_gradient of
+ * Algorithm 2/3), learning rate eta_t = eta_0 / (1 + mu t).
+ *
+ * Conventions for every call
+ *   - Indices are 0-based int32.  Tensors are given structure-of-arrays: idx[n] points
+ *     to the n-th index of every entry.
+ *   - Factor matrices are dense row-major (I_n x J_n, K_m x J_c); the core is dense
+ *     J_1 x ... x J_N with the last mode fastest.  All parameter buffers the caller
+ *     passes are FP32 and unpadded.
+ *   - "device" pointers are CUDA device (or managed) memory of the context's device;
+ *     "host" pointers are ordinary (preferably pinned) host memory.
+ *   - Inputs are owned by the caller and only read during the call.  The library keeps
+ *     its own copies; nothing it allocates is handed to the caller.
+ *   - All device work is ordered on the stream given to s3_init.  Calls that return a
+ *     scalar to the host (s3_loss, s3_rmse) synchronise that stream; the others only
+ *     enqueue work, except where stated.
+ *   - Every call returns S3_OK or a negative status.  Invalid arguments and out-of-range
+ *     indices are detected on the host before any kernel runs; no input can make a
+ *     kernel fault.  After S3_ERR_CUDA the context is marked failed and every later call
+ *     returns S3_ERR_STATE; s3_last_error() gives the text of the last error.
+ */
+#ifndef S3CMTF_H_
+#define S3CMTF_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct s3_ctx s3_ctx;  /* opaque, owned by the library */
+
+enum {
+    S3_OK = 0,
+    S3_ERR_ARG = -1,       /* invalid argument, shape or unsupported configuration */
+    S3_ERR_INDEX = -2,     /* an index outside its mode's range */
+    S3_ERR_OOM = -3,       /* device or host allocation failed */
+    S3_ERR_CUDA = -4,      /* a CUDA runtime error; the context is unusable afterwards */
+    S3_ERR_DIVERGED = -5,  /* a non-finite parameter or loss was produced */
+    S3_ERR_STATE = -6      /* NULL, destroyed or failed context */
+};
+
+enum { S3_MINIBATCH = 0, S3_HOGWILD = 1 };         /* epoch modes */
+enum { S3_FP32 = 0, S3_BF16 = 1 };                 /* precision forms */
+enum { S3_ROW_SUM = 0, S3_ROW_MEAN = 1 };          /* row rule of a group step */
+
+/* Observed tensor entries Omega_X with their values (Section 2.3, Definition 2). */
+typedef struct {
+    int n_modes;                 /* N, 3 or 4 */
+    const int64_t* dims;         /* host [N]: I_1..I_N */
+    int64_t nnz;                 /* |Omega_X| */
+    const int32_t* const* idx;   /* host array of N pointers, each [nnz] (host or device) */
+    const float* val;            /* [nnz] (host or device) */
+} s3_coo_tensor;
+
+/* Observed entries of a matrix Y (I_c x K) coupled to tensor mode coupled_mode
+   (Definition 1); its factor is V (K x J_c). */
+typedef struct {
+    int coupled_mode;            /* c, 0-based tensor mode */
+    int64_t rows;                /* I_c (must equal dims[c]) */
+    int64_t cols;                /* K */
+    int64_t nnz;                 /* |Omega_Y| */
+    const int32_t* r;            /* [nnz] row index j1 in [0, I_c) */
+    const int32_t* c;            /* [nnz] column index j2 in [0, K) */
+    const float* val;            /* [nnz]; NULL means every stored entry is 1 */
+} s3_coo_matrix;
+
+/* Hyper-parameters (Section 4.1 "Parameters"; the GPU group rules are this library's). */
+typedef struct {
+    float lr0;          /* eta_0 */
+    float mu;           /* decay: eta_t = eta_0 / (1 + mu t), t = 0-based epoch */
+    float lambda_reg;   /* regularisation of factors and core */
+    float lambda_m;     /* weight of the coupled-matrix terms */
+    int batch;          /* minibatch size B (items of the visiting order per step) */
+    float core_scale;   /* core step = eta_t * core_scale * (mean core gradient of a group) */
+    int row_rule;       /* S3_ROW_SUM or S3_ROW_MEAN: a row takes the sum, or the mean, of
+                           its gradients within one group (batch or HOGWILD tile) */
+    int hog_tile;       /* HOGWILD: tensor entries per tile (0 = default 256) */
+    int64_t hog_round;  /* HOGWILD: tensor entries between core updates (0 = default) */
+} s3_hparams;
+
+/* Create a context on the current CUDA device.
+ *   train        tensor entries to fit (values FP32)
+ *   Y, n_coupled coupled matrices (n_coupled may be 0, then Y may be NULL); at most 8
+ *   J            host [N] core dimensionalities J_n (1..32)
+ *   hp           hyper-parameters (copied)
+ *   seed         seeds the initial parameters (factors and coupled factors U(0,1); core
+ *                N(0, 3^N / prod J)), drawn by a counter-based generator (splitmix64)
+ *                and, when order is NULL, the visiting order
+ *   order        NULL, or [nnz + sum of coupled nnz] int64: the visiting order of the
+ *                union of items (item k < nnz is tensor entry k; then the entries of each
+ *                coupled matrix in turn) -- Algorithm 1 visits them "in random order"
+ *   device_ptrs  0: every array above is host memory; 1: idx/val/r/c/val/order are
+ *                device memory
+ *   stream       cudaStream_t to order all work on (NULL = legacy default stream)
+ * The entries are validated (range, finiteness), reordered into the library's layout
+ * (visiting order, grouped into minibatches and HOGWILD tiles, each group's row
+ * occurrences sorted into segments) and uploaded once.  Blocks until the layout is built.
+ * On failure *out may still receive a context in the failed state so that
+ * s3_last_error() can explain the status; release it with s3_destroy().
+ */
+int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y, int n_coupled,
+            const int* J, const s3_hparams* hp, uint64_t seed, const int64_t* order,
+            int device_ptrs, void* stream);
+
+/* One pass over all items at eta_t, t = the context's epoch counter, which then advances.
+ *   mode       S3_MINIBATCH: consecutive groups of hp.batch items of the visiting order;
+ *              every gradient of a group is taken at the group-start parameters, rows
+ *              take -eta_t * (sum or mean) of their Eq. (8) gradients, the core takes
+ *              -eta_t * core_scale * (mean of its Eq. (8) gradients); deterministic.
+ *              S3_HOGWILD: the lock-free scheme of Section 3.3 on the GPU: tiles of the
+ *              visiting order run concurrently, each reading the current rows, combining
+ *              its gradients per row (row_rule) and adding the step atomically; the core
+ *              is read-only within a round of hp.hog_round tensor entries and then takes
+ *              one step with the round's mean core gradient (the GPU counterpart of the
+ *              paper's "core updated by one worker"); not deterministic.
+ *   precision  S3_FP32 (CUDA-core FP32), or S3_BF16 (tensor-core contraction with BF16
+ *              operands and FP32 accumulation; FP32 master parameters and errors).
+ * Returns S3_ERR_DIVERGED if a non-finite parameter appeared (the parameters are left as
+ * they are).  Enqueues work and synchronises once at the end to read the flag. */
+int s3_epoch(s3_ctx* ctx, int mode, int precision);
+
+/* f of Eq. (7) at the current parameters (FP32 errors, compensated FP32 partial sums,
+ * FP64 final reduction), and the RMSE over the train entries.  Either output may be
+ * NULL.  Synchronises. */
+int s3_loss(s3_ctx* ctx, double* f_out, double* train_rmse_out);
+
+/* test RMSE of Section 4.1 over the given entries (no clipping).  test == NULL uses the
+ * entries given to the last s3_set_test.  Host or device pointers per device_ptrs.
+ * Synchronises. */
+int s3_rmse(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs, double* rmse_out);
+
+/* Keep a copy of test entries on the device for s3_rmse(ctx, NULL, ...). */
+int s3_set_test(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs);
+
+/* Predictions x~ (Eq. (4)) at n coordinates: idx = host array of N device pointers each
+ * [n]; out = device [n] FP32. */
+int s3_predict(s3_ctx* ctx, const int32_t* const* idx, int64_t n, float* out);
+
+/* Full gradient of f (sum over all train and coupled entries of Eq. (8)) at the current
+ * parameters, written to caller-owned device buffers of the parameter shapes:
+ * dG [prod J], dU[n] [I_n * J_n], dV[m] [K_m * J_c].  Rows without observed entries get
+ * zero.  Deterministic (fixed-order segmented reductions with compensated FP32 sums). */
+int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* const* dV);
+
+/* Copy the parameters out to / in from caller-owned device buffers (shapes as above).
+ * Used for checkpoint/resume (with s3_set_epoch) and to inject parameters. */
+int s3_get_params(s3_ctx* ctx, float* G, float* const* U, float* const* V);
+int s3_set_params(s3_ctx* ctx, const float* G, const float* const* U, const float* const* V);
+
+/* Epoch counter t used for eta_t (read and set; resume = set_params + set_epoch). */
+int s3_get_epoch(s3_ctx* ctx, int64_t* t);
+int s3_set_epoch(s3_ctx* ctx, int64_t t);
+
+/* Replace the observed values (not the coordinates) from HOST memory: the tensor's
+ * values in the order given to s3_init and each coupled matrix's values likewise
+ * (y_val may be NULL when n_coupled is 0; an entry y_val[m] may be NULL to keep that
+ * matrix).  The host-to-device copy and the scatter into the library's layout are
+ * enqueued on the stream; host buffers must stay valid until the stream reaches them. */
+int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val);
+
+/* Sizes: number of items in the visiting order, groups per epoch for each mode. */
+int s3_info(s3_ctx* ctx, int64_t* n_union, int64_t* n_batches, int64_t* n_tiles);
+
+/* Measurement support.  s3_profile(ctx, 1) makes the library record CUDA events on its
+ * stream around every launch of its dominant kernels and count every kernel it launches;
+ * s3_profile(ctx, 0) stops; enabling again clears the counters.  s3_profile_read gives,
+ * for a kernel family, the summed event time of its launches (ms, synchronises), the
+ * number of its launches and the tensor entries they processed; family -1 gives the
+ * number of kernel launches of every kind (ms and entries 0).  Families:
+ *   S3_K_TENSOR_HOG (HOGWILD tensor pass), S3_K_TENSOR_MB (minibatch tensor pass, only
+ *   when profiling: the minibatch epoch is then launched without its CUDA graph),
+ *   S3_K_TENSOR_GRAD (gradient tensor pass), S3_K_TENSOR_FWD (loss / RMSE / predict). */
+enum { S3_K_ALL = -1, S3_K_TENSOR_HOG = 0, S3_K_TENSOR_MB = 1, S3_K_TENSOR_GRAD = 2,
+       S3_K_TENSOR_FWD = 3 };
+int s3_profile(s3_ctx* ctx, int enable);
+int s3_profile_read(s3_ctx* ctx, int family, double* ms, int64_t* launches, int64_t* entries);
+
+const char* s3_last_error(const s3_ctx* ctx);
+void s3_destroy(s3_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* S3CMTF_H_ */

@@ -1,0 +1,887 @@
+// C ABI of the S3CMTF sm_103a path (declared in include/s3cmtf.h).  Host code: argument
+// validation, the layout build, device buffers and the launch sequence of each call.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "layout.h"
+#include "s3cmtf.h"
+
+using namespace s3;
+
+static constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
+
+namespace {
+
+// device copy of one grouping plus the host metadata needed to size launches
+struct DevGrouping {
+    DGroup d{};
+    int64_t ngroups = 0;
+    int nF = 0;
+    std::vector<int64_t> t_off, c_off[kMaxM], seg_off[kMaxF], slot_off[kMaxF];
+    int64_t max_t = 0, max_c[kMaxM] = {}, max_seg[kMaxF] = {}, max_ev[kMaxF] = {};
+    int64_t* t_src = nullptr;
+    int64_t* c_src[kMaxM] = {};
+    float* tval = nullptr;          // mutable aliases of d.tval / d.cval
+    float* cval[kMaxM] = {};
+};
+
+}  // namespace
+
+struct s3_ctx {
+    int N = 0, M = 0, JP = 0, JPR = 0;
+    int64_t I[kMaxN] = {};
+    int J[kMaxN] = {};
+    int cmode[kMaxM] = {};
+    int64_t K[kMaxM] = {};
+    int64_t nnz = 0, ynnz[kMaxM] = {}, n_union = 0;
+    s3_hparams hp{};
+    uint64_t seed = 0;
+    int64_t epoch = 0;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    bool failed = false;
+    std::string err;
+    std::vector<void*> allocs;
+    DParams P{};
+    float* inv_cnt[kMaxF] = {};
+    DevGrouping mb, hog, grad;
+    float* contrib[kMaxF] = {};
+    float* core_part = nullptr;
+    int64_t core_part_n = 0;       // partial slots
+    float* red_parts = nullptr;
+    int64_t red_parts_n = 0;       // float pairs
+    double* d_red = nullptr;
+    double* h_red = nullptr;       // pinned
+    float* d_eta = nullptr;
+    float* h_eta = nullptr;        // pinned
+    int* d_flag = nullptr;
+    int* h_flag = nullptr;         // pinned
+    float* grad_comp = nullptr;    // compensation buffers of the gradient (all parameters)
+    int64_t grad_comp_n = 0;
+    float* values_stage = nullptr; // s3_update_values staging (nnz + sum ynnz floats)
+    int64_t ntest = 0;
+    int32_t* test_idx[kMaxN] = {};
+    float* test_val = nullptr;
+    int64_t hog_round_tiles = 0;
+    size_t hog_smem = 0;
+    cudaGraphExec_t mb_graph = nullptr;
+    // measurement (s3_profile)
+    bool prof = false;
+    int64_t launches = 0;
+    struct Family {
+        std::vector<cudaEvent_t> ev;   // start/stop pairs
+        int64_t launches = 0, entries = 0;
+    } fam[4];
+};
+
+// ------------------------------------------------------------------ helpers
+static int fail(s3_ctx* c, int code, const std::string& msg) {
+    if (c) {
+        c->err = msg;
+        if (code == S3_ERR_CUDA) c->failed = true;
+    }
+    return code;
+}
+
+#define CK(expr)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? S3_ERR_OOM : S3_ERR_CUDA,  \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+    } while (0)
+
+// a kernel launch of the library: counted, errors handled like CK
+#define KL(expr)             \
+    do {                     \
+        ctx->launches += 1;  \
+        CK(expr);            \
+    } while (0)
+
+// CUDA events around one launch of a measured kernel family (only while profiling)
+static cudaError_t prof_mark(s3_ctx* ctx, int family) {
+    if (!ctx->prof) return cudaSuccess;
+    cudaEvent_t e;
+    cudaError_t r = cudaEventCreate(&e);
+    if (r != cudaSuccess) return r;
+    ctx->fam[family].ev.push_back(e);
+    return cudaEventRecord(e, ctx->stream);
+}
+static void prof_count(s3_ctx* ctx, int family, int64_t entries) {
+    if (!ctx->prof) return;
+    ctx->fam[family].launches += 1;
+    ctx->fam[family].entries += entries;
+}
+
+template <typename T>
+static cudaError_t dalloc(s3_ctx* ctx, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess) ctx->allocs.push_back(*p);
+    return e;
+}
+
+template <typename T>
+static cudaError_t upload(s3_ctx* ctx, T** p, const std::vector<T>& v) {
+    cudaError_t e = dalloc(ctx, p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+}
+
+static bool usable(const s3_ctx* c) { return c && !c->failed; }
+
+static float eta_of(const s3_ctx* c, int64_t t) {
+    return (float)((double)c->hp.lr0 / (1.0 + (double)c->hp.mu * (double)t));
+}
+
+static int upload_grouping(s3_ctx* ctx, const HostGrouping& H, DevGrouping& D) {
+    D.ngroups = H.ngroups;
+    D.nF = H.nF;
+    D.t_off = H.t_off;
+    D.max_t = H.max_t;
+    int64_t* toff = nullptr;
+    CK(upload(ctx, &toff, H.t_off));
+    D.d.t_off = toff;
+    for (int n = 0; n < ctx->N; ++n) {
+        int32_t *a = nullptr, *b = nullptr;
+        CK(upload(ctx, &a, H.tidx[n]));
+        CK(upload(ctx, &b, H.tpos[n]));
+        D.d.tidx[n] = a;
+        D.d.tpos[n] = b;
+    }
+    CK(upload(ctx, &D.tval, H.tval));
+    D.d.tval = D.tval;
+    CK(upload(ctx, &D.t_src, H.t_src));
+    for (int m = 0; m < ctx->M; ++m) {
+        D.c_off[m] = H.c_off[m];
+        D.max_c[m] = H.max_c[m];
+        int64_t* co = nullptr;
+        int32_t *r = nullptr, *c = nullptr, *pu = nullptr, *pv = nullptr;
+        CK(upload(ctx, &co, H.c_off[m]));
+        CK(upload(ctx, &r, H.cr[m]));
+        CK(upload(ctx, &c, H.cc[m]));
+        CK(upload(ctx, &D.cval[m], H.cval[m]));
+        CK(upload(ctx, &pu, H.cpos_u[m]));
+        CK(upload(ctx, &pv, H.cpos_v[m]));
+        CK(upload(ctx, &D.c_src[m], H.c_src[m]));
+        D.d.c_off[m] = co;
+        D.d.cr[m] = r;
+        D.d.cc[m] = c;
+        D.d.cval[m] = D.cval[m];
+        D.d.cpos_u[m] = pu;
+        D.d.cpos_v[m] = pv;
+    }
+    for (int F = 0; F < H.nF; ++F) {
+        D.seg_off[F] = H.seg_off[F];
+        D.slot_off[F] = H.slot_off[F];
+        D.max_seg[F] = H.max_seg[F];
+        D.max_ev[F] = H.max_ev[F];
+        int64_t *so = nullptr, *sl = nullptr;
+        int32_t *sr = nullptr, *ss = nullptr, *sc = nullptr;
+        CK(upload(ctx, &so, H.seg_off[F]));
+        CK(upload(ctx, &sl, H.slot_off[F]));
+        CK(upload(ctx, &sr, H.seg_row[F]));
+        CK(upload(ctx, &ss, H.seg_start[F]));
+        CK(upload(ctx, &sc, H.seg_cnt[F]));
+        D.d.seg_off[F] = so;
+        D.d.slot_off[F] = sl;
+        D.d.seg_row[F] = sr;
+        D.d.seg_start[F] = ss;
+        D.d.seg_cnt[F] = sc;
+    }
+    // keep the host vectors alive until the async copies are done
+    CK(cudaStreamSynchronize(ctx->stream));
+    return S3_OK;
+}
+
+static void fill_params(s3_ctx* ctx) {
+    DParams& P = ctx->P;
+    P.N = ctx->N;
+    P.M = ctx->M;
+    P.ld = ctx->JPR;
+    P.ldg = ctx->JPR;
+    for (int m = 0; m < ctx->M; ++m) P.cmode[m] = ctx->cmode[m];
+    for (int F = 0; F < ctx->N + ctx->M; ++F) P.inv_cnt[F] = ctx->inv_cnt[F];
+    P.lambda_reg = ctx->hp.lambda_reg;
+    P.lambda_m = ctx->hp.lambda_m;
+    P.inv_nnz = (float)(1.0 / (double)ctx->nnz);
+}
+
+static int64_t factor_rows(const s3_ctx* ctx, int F) {
+    return F < ctx->N ? ctx->I[F] : ctx->K[F - ctx->N];
+}
+static int factor_cols(const s3_ctx* ctx, int F) {
+    return F < ctx->N ? ctx->J[F] : ctx->J[ctx->cmode[F - ctx->N]];
+}
+static float* factor_ptr(const s3_ctx* ctx, int F) {
+    return F < ctx->N ? ctx->P.U[F] : ctx->P.V[F - ctx->N];
+}
+
+// reads a host-or-device array into a host vector
+template <typename T>
+static cudaError_t to_host(const T* p, int64_t n, int device_ptrs, std::vector<T>& out) {
+    out.resize((size_t)n);
+    if (n == 0) return cudaSuccess;
+    if (device_ptrs) return cudaMemcpy(out.data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost);
+    memcpy(out.data(), p, (size_t)n * sizeof(T));
+    return cudaSuccess;
+}
+
+static int ensure_red(s3_ctx* ctx, int64_t pairs) {
+    if (pairs <= ctx->red_parts_n) return S3_OK;
+    if (ctx->red_parts) cudaFree(ctx->red_parts);
+    ctx->allocs.erase(std::remove(ctx->allocs.begin(), ctx->allocs.end(), (void*)ctx->red_parts),
+                      ctx->allocs.end());
+    CK(dalloc(ctx, &ctx->red_parts, (size_t)pairs * 2));
+    ctx->red_parts_n = pairs;
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ init
+extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y,
+                       int n_coupled, const int* J, const s3_hparams* hp, uint64_t seed,
+                       const int64_t* order, int device_ptrs, void* stream) {
+    if (!out) return S3_ERR_ARG;
+    *out = nullptr;
+    s3_ctx* ctx = new s3_ctx();
+    auto bail = [&](int code, const std::string& m) {
+        // keep the context so the caller can read the message; it is marked failed
+        ctx->err = m;
+        ctx->failed = true;
+        *out = ctx;
+        return code;
+    };
+    if (!train || !J || !hp) return bail(S3_ERR_ARG, "train, J and hp are required");
+    const int N = train->n_modes;
+    if (N != 3 && N != 4) return bail(S3_ERR_ARG, "n_modes must be 3 or 4");
+    if (n_coupled < 0 || n_coupled > kMaxM) return bail(S3_ERR_ARG, "n_coupled must be 0..8");
+    if (n_coupled > 0 && !Y) return bail(S3_ERR_ARG, "Y is NULL but n_coupled > 0");
+    if (!train->dims || !train->idx || !train->val) return bail(S3_ERR_ARG, "train arrays missing");
+    if (train->nnz < 1) return bail(S3_ERR_ARG, "train needs at least one entry");
+    if (train->nnz > INT32_MAX) return bail(S3_ERR_ARG, "more than 2^31-1 train entries");
+    ctx->N = N;
+    ctx->M = n_coupled;
+    ctx->hp = *hp;
+    ctx->seed = seed;
+    ctx->nnz = train->nnz;
+    ctx->stream = (cudaStream_t)stream;
+    int Jmax = 0;
+    for (int n = 0; n < N; ++n) {
+        ctx->I[n] = train->dims[n];
+        ctx->J[n] = J[n];
+        if (ctx->I[n] < 1 || ctx->I[n] > INT32_MAX) return bail(S3_ERR_ARG, "dims out of range");
+        if (J[n] < 1 || J[n] > 32) return bail(S3_ERR_ARG, "J_n must be in 1..32");
+        Jmax = std::max(Jmax, J[n]);
+    }
+    ctx->JP = tensor_supported_jp(N, Jmax);
+    if (!ctx->JP) return bail(S3_ERR_ARG, "unsupported rank for this order (N=4 supports J<=8)");
+    ctx->JPR = round4(ctx->JP);
+    if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
+        !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
+        hp->hog_tile < 0 || hp->hog_round < 0)
+        return bail(S3_ERR_ARG, "invalid hyper-parameters");
+    for (int m = 0; m < n_coupled; ++m) {
+        const s3_coo_matrix& y = Y[m];
+        if (y.coupled_mode < 0 || y.coupled_mode >= N) return bail(S3_ERR_ARG, "coupled_mode out of range");
+        if (y.rows != ctx->I[y.coupled_mode]) return bail(S3_ERR_ARG, "coupled rows != dims[coupled_mode]");
+        if (y.cols < 1 || y.cols > INT32_MAX) return bail(S3_ERR_ARG, "coupled cols out of range");
+        if (y.nnz < 0 || (y.nnz > 0 && (!y.r || !y.c))) return bail(S3_ERR_ARG, "coupled arrays missing");
+        ctx->cmode[m] = y.coupled_mode;
+        ctx->K[m] = y.cols;
+        ctx->ynnz[m] = y.nnz;
+    }
+    ctx->n_union = ctx->nnz;
+    for (int m = 0; m < n_coupled; ++m) ctx->n_union += ctx->ynnz[m];
+    // ---- bring the inputs to the host and validate them
+    HostInput in;
+    in.N = N;
+    in.M = n_coupled;
+    in.nnz = ctx->nnz;
+    std::vector<int32_t> hidx[kMaxN], hyr[kMaxM], hyc[kMaxM];
+    std::vector<float> hval, hyv[kMaxM];
+    std::vector<int64_t> hord;
+    {
+        cudaError_t e = cudaSuccess;
+        for (int n = 0; n < N && e == cudaSuccess; ++n) e = to_host(train->idx[n], ctx->nnz, device_ptrs, hidx[n]);
+        if (e == cudaSuccess) e = to_host(train->val, ctx->nnz, device_ptrs, hval);
+        for (int m = 0; m < n_coupled && e == cudaSuccess; ++m) {
+            e = to_host(Y[m].r, Y[m].nnz, device_ptrs, hyr[m]);
+            if (e == cudaSuccess) e = to_host(Y[m].c, Y[m].nnz, device_ptrs, hyc[m]);
+            if (e == cudaSuccess) {
+                if (Y[m].val) e = to_host(Y[m].val, Y[m].nnz, device_ptrs, hyv[m]);
+                else hyv[m].assign((size_t)Y[m].nnz, 1.0f);
+            }
+        }
+        if (e == cudaSuccess && order) e = to_host(order, ctx->n_union, device_ptrs, hord);
+        if (e != cudaSuccess) return bail(S3_ERR_ARG, std::string("reading inputs: ") + cudaGetErrorString(e));
+    }
+    for (int n = 0; n < N; ++n) {
+        for (int64_t e = 0; e < ctx->nnz; ++e) {
+            const int32_t v = hidx[n][(size_t)e];
+            if (v < 0 || v >= ctx->I[n])
+                return bail(S3_ERR_INDEX, "tensor index out of range: mode " + std::to_string(n) +
+                                              ", entry " + std::to_string(e));
+        }
+        in.I[n] = ctx->I[n];
+        in.idx[n] = hidx[n].data();
+    }
+    for (int64_t e = 0; e < ctx->nnz; ++e)
+        if (!std::isfinite(hval[(size_t)e])) return bail(S3_ERR_ARG, "non-finite tensor value at " + std::to_string(e));
+    in.val = hval.data();
+    for (int m = 0; m < n_coupled; ++m) {
+        for (int64_t b = 0; b < ctx->ynnz[m]; ++b) {
+            if (hyr[m][(size_t)b] < 0 || hyr[m][(size_t)b] >= Y[m].rows || hyc[m][(size_t)b] < 0 ||
+                hyc[m][(size_t)b] >= Y[m].cols)
+                return bail(S3_ERR_INDEX, "coupled index out of range: matrix " + std::to_string(m) +
+                                              ", entry " + std::to_string(b));
+            if (!std::isfinite(hyv[m][(size_t)b])) return bail(S3_ERR_ARG, "non-finite coupled value");
+        }
+        in.cmode[m] = ctx->cmode[m];
+        in.K[m] = ctx->K[m];
+        in.ynnz[m] = ctx->ynnz[m];
+        in.yr[m] = hyr[m].data();
+        in.yc[m] = hyc[m].data();
+        in.yv[m] = hyv[m].data();
+    }
+    if (order) {
+        std::vector<uint8_t> seen((size_t)ctx->n_union, 0);
+        for (int64_t k = 0; k < ctx->n_union; ++k) {
+            const int64_t v = hord[(size_t)k];
+            if (v < 0 || v >= ctx->n_union || seen[(size_t)v])
+                return bail(S3_ERR_INDEX, "order is not a permutation of the items");
+            seen[(size_t)v] = 1;
+        }
+    } else {
+        seeded_order(seed, ctx->n_union, hord);
+    }
+    // ---- layouts
+    HostGrouping hmb, hhog, hgrad;
+    const int64_t tile = hp->hog_tile > 0 ? std::min(hp->hog_tile, kTile) : kTile;
+    std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb);
+    if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SEG, hhog);
+    const int64_t grad_chunk = 1 << 20;
+    if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad);
+    if (!msg.empty()) return bail(S3_ERR_ARG, msg);
+    {
+        cudaError_t e = cudaGetDevice(&ctx->device);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+        if (e != cudaSuccess) return bail(S3_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    }
+    *out = ctx;
+    // ---- device buffers
+    const int nF = N + n_coupled;
+    for (int n = 0; n < N; ++n) {
+        CK(dalloc(ctx, &ctx->P.U[n], (size_t)ctx->I[n] * ctx->JPR));
+        CK(cudaMemsetAsync(ctx->P.U[n], 0, (size_t)ctx->I[n] * ctx->JPR * sizeof(float), ctx->stream));
+    }
+    for (int m = 0; m < n_coupled; ++m) {
+        CK(dalloc(ctx, &ctx->P.V[m], (size_t)ctx->K[m] * ctx->JPR));
+        CK(cudaMemsetAsync(ctx->P.V[m], 0, (size_t)ctx->K[m] * ctx->JPR * sizeof(float), ctx->stream));
+    }
+    {
+        size_t q = 1;
+        for (int n = 0; n < N - 1; ++n) q *= ctx->JP;
+        CK(dalloc(ctx, &ctx->P.G, q * ctx->JPR));
+        CK(cudaMemsetAsync(ctx->P.G, 0, q * ctx->JPR * sizeof(float), ctx->stream));
+    }
+    // per-row inverse counts from the train entries (|Omega^{n,i}|, |Omega_Y^{2,k}|)
+    for (int F = 0; F < nF; ++F) {
+        const int64_t rows = factor_rows(ctx, F);
+        std::vector<int64_t> cnt((size_t)rows, 0);
+        if (F < N) for (int64_t e = 0; e < ctx->nnz; ++e) cnt[(size_t)hidx[F][(size_t)e]]++;
+        else for (int64_t b = 0; b < ctx->ynnz[F - N]; ++b) cnt[(size_t)hyc[F - N][(size_t)b]]++;
+        std::vector<float> inv((size_t)rows);
+        for (int64_t i = 0; i < rows; ++i) inv[(size_t)i] = cnt[(size_t)i] ? (float)(1.0 / (double)cnt[(size_t)i]) : 0.f;
+        CK(upload(ctx, &ctx->inv_cnt[F], inv));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    fill_params(ctx);
+    int rc;
+    if ((rc = upload_grouping(ctx, hmb, ctx->mb)) != S3_OK) return rc;
+    if ((rc = upload_grouping(ctx, hhog, ctx->hog)) != S3_OK) return rc;
+    if ((rc = upload_grouping(ctx, hgrad, ctx->grad)) != S3_OK) return rc;
+    // scratch: contribution slots (minibatch and gradient groups), core partials
+    for (int F = 0; F < nF; ++F) {
+        const int64_t ev = std::max(ctx->mb.max_ev[F], ctx->grad.max_ev[F]);
+        CK(dalloc(ctx, &ctx->contrib[F], (size_t)std::max<int64_t>(ev, 1) * ctx->JPR));
+    }
+    {
+        int64_t pd = 1;
+        for (int n = 0; n < N; ++n) pd *= ctx->JP;
+        const int64_t parts = std::max<int64_t>({(ctx->mb.max_t + kTile - 1) / kTile,
+                                                 (ctx->grad.max_t + kTile - 1) / kTile,
+                                                 (int64_t)ctx->num_sms * 8, 1});
+        ctx->core_part_n = parts;
+        CK(dalloc(ctx, &ctx->core_part, (size_t)(parts * pd)));
+    }
+    CK(dalloc(ctx, &ctx->d_red, 64));
+    CK(cudaMallocHost((void**)&ctx->h_red, 64 * sizeof(double)));
+    CK(dalloc(ctx, &ctx->d_eta, 1));
+    CK(cudaMallocHost((void**)&ctx->h_eta, sizeof(float)));
+    CK(dalloc(ctx, &ctx->d_flag, 1));
+    CK(cudaMallocHost((void**)&ctx->h_flag, sizeof(int)));
+    ctx->hog_smem = tensor_hog_smem(N, ctx->JP, ctx->hog.max_seg, nF);
+    CK(tensor_prepare(N, ctx->JP, ctx->hog_smem <= kMaxSmem ? ctx->hog_smem : 0));
+    const int64_t round = hp->hog_round > 0 ? hp->hog_round : (int64_t)1 << 16;
+    ctx->hog_round_tiles = std::max<int64_t>(1, (round + tile - 1) / tile);
+    // initial parameters
+    KL(launch_init_params(ctx->P, ctx->I, ctx->J, ctx->K, ctx->JP, seed, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return S3_OK;
+}
+
+static void free_coo(int32_t** idx, float** val) {
+    for (int k = 0; k < kMaxN; ++k) {
+        if (idx[k]) cudaFree(idx[k]);
+        idx[k] = nullptr;
+    }
+    if (*val) cudaFree(*val);
+    *val = nullptr;
+}
+
+static void prof_clear(s3_ctx* ctx) {
+    for (auto& f : ctx->fam) {
+        for (cudaEvent_t e : f.ev) cudaEventDestroy(e);
+        f.ev.clear();
+        f.launches = 0;
+        f.entries = 0;
+    }
+    ctx->launches = 0;
+}
+
+extern "C" void s3_destroy(s3_ctx* ctx) {
+    if (!ctx) return;
+    if (ctx->mb_graph) cudaGraphExecDestroy(ctx->mb_graph);
+    prof_clear(ctx);
+    free_coo(ctx->test_idx, &ctx->test_val);
+    cudaStreamSynchronize(ctx->stream);
+    for (void* p : ctx->allocs) cudaFree(p);
+    if (ctx->h_red) cudaFreeHost(ctx->h_red);
+    if (ctx->h_eta) cudaFreeHost(ctx->h_eta);
+    if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+    delete ctx;
+}
+
+extern "C" int s3_profile(s3_ctx* ctx, int enable) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (enable) prof_clear(ctx);
+    ctx->prof = enable != 0;
+    return S3_OK;
+}
+
+extern "C" int s3_profile_read(s3_ctx* ctx, int family, double* ms, int64_t* launches,
+                               int64_t* entries) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (family < -1 || family > 3) return fail(ctx, S3_ERR_ARG, "unknown kernel family");
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (family == -1) {
+        if (ms) *ms = 0.0;
+        if (launches) *launches = ctx->launches;
+        if (entries) *entries = 0;
+        return S3_OK;
+    }
+    auto& f = ctx->fam[family];
+    double total = 0.0;
+    for (size_t k = 0; k + 1 < f.ev.size(); k += 2) {
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, f.ev[k], f.ev[k + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = f.launches;
+    if (entries) *entries = f.entries;
+    return S3_OK;
+}
+
+extern "C" const char* s3_last_error(const s3_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : "NULL context";
+}
+
+// ------------------------------------------------------------------ epoch
+static int enqueue_minibatch(s3_ctx* ctx) {
+    const int N = ctx->N, M = ctx->M, nF = N + M;
+    DevGrouping& D = ctx->mb;
+    const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
+    for (int64_t g = 0; g < D.ngroups; ++g) {
+        TensorLaunch L{};
+        L.e_begin = D.t_off[(size_t)g];
+        L.e_end = D.t_off[(size_t)g + 1];
+        for (int n = 0; n < N; ++n) L.contrib[n] = ctx->contrib[n];
+        L.core_part = ctx->core_part;
+        CK(prof_mark(ctx, S3_K_TENSOR_MB));
+        KL(launch_tensor_contrib(N, ctx->JP, ctx->P, D.d, L, ctx->stream));
+        CK(prof_mark(ctx, S3_K_TENSOR_MB));
+        prof_count(ctx, S3_K_TENSOR_MB, L.e_end - L.e_begin);
+        for (int m = 0; m < M; ++m)
+            KL(launch_coupled_contrib(ctx->P, D.d, m, D.c_off[m][(size_t)g], D.c_off[m][(size_t)g + 1],
+                                      ctx->contrib[ctx->cmode[m]], ctx->contrib[N + m], ctx->stream));
+        SegmentLaunch S{};
+        S.nF = nF;
+        S.g = g;
+        S.seg_begin[0] = 0;
+        for (int F = 0; F < nF; ++F) {
+            S.contrib[F] = ctx->contrib[F];
+            S.seg_begin[F + 1] = S.seg_begin[F] + (D.seg_off[F][(size_t)g + 1] - D.seg_off[F][(size_t)g]);
+        }
+        S.total_segs = S.seg_begin[nF];
+        KL(launch_segments(ctx->P, D.d, S, ctx->d_eta, row_mean, 0, ctx->stream));
+        const int64_t nt = L.e_end - L.e_begin;
+        KL(launch_core(ctx->P, N, ctx->JP, ctx->J, ctx->core_part, (nt + kTile - 1) / kTile, nt,
+                       ctx->d_eta, ctx->hp.core_scale, 0, nullptr, nullptr, ctx->stream));
+    }
+    return S3_OK;
+}
+
+static int enqueue_hogwild(s3_ctx* ctx) {
+    DevGrouping& D = ctx->hog;
+    if (ctx->hog_smem > kMaxSmem)
+        return fail(ctx, S3_ERR_ARG, "a HOGWILD tile needs " + std::to_string(ctx->hog_smem) +
+                                         " bytes of shared memory; lower hog_tile");
+    const int nF = ctx->N + ctx->M;
+    const size_t smem = tensor_hog_smem(ctx->N, ctx->JP, D.max_seg, nF);
+    const int per_sm = std::max(1, tensor_hog_blocks_per_sm(ctx->N, ctx->JP, smem));
+    const int64_t cap = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, ctx->core_part_n);
+    const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
+    for (int64_t t0 = 0; t0 < D.ngroups; t0 += ctx->hog_round_tiles) {
+        const int64_t t1 = std::min(D.ngroups, t0 + ctx->hog_round_tiles);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t1 - t0, cap));
+        const int64_t nt = D.t_off[(size_t)t1] - D.t_off[(size_t)t0];
+        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+        KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->P, D.d, t0, t1, grid, ctx->d_eta, row_mean,
+                             ctx->core_part, D.max_seg, ctx->stream));
+        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+        prof_count(ctx, S3_K_TENSOR_HOG, nt);
+        KL(launch_core(ctx->P, ctx->N, ctx->JP, ctx->J, ctx->core_part, grid, nt, ctx->d_eta,
+                       ctx->hp.core_scale, 0, nullptr, nullptr, ctx->stream));
+    }
+    return S3_OK;
+}
+
+static int check_params_finite(s3_ctx* ctx, bool* bad) {
+    CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), ctx->stream));
+    size_t q = 1;
+    for (int n = 0; n < ctx->N - 1; ++n) q *= ctx->JP;
+    KL(launch_check_finite(ctx->P.G, (int64_t)(q * ctx->JPR), ctx->d_flag, ctx->stream));
+    for (int F = 0; F < ctx->N + ctx->M; ++F)
+        KL(launch_check_finite(factor_ptr(ctx, F), factor_rows(ctx, F) * ctx->JPR, ctx->d_flag, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *bad = *ctx->h_flag != 0;
+    return S3_OK;
+}
+
+extern "C" int s3_epoch(s3_ctx* ctx, int mode, int precision) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (mode != S3_MINIBATCH && mode != S3_HOGWILD) return fail(ctx, S3_ERR_ARG, "unknown mode");
+    if (precision != S3_FP32 && precision != S3_BF16) return fail(ctx, S3_ERR_ARG, "unknown precision");
+    if (precision == S3_BF16) return fail(ctx, S3_ERR_ARG, "BF16 form not built for this configuration");
+    *ctx->h_eta = eta_of(ctx, ctx->epoch);
+    CK(cudaMemcpyAsync(ctx->d_eta, ctx->h_eta, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    int rc;
+    if (mode == S3_MINIBATCH && ctx->prof) {
+        if ((rc = enqueue_minibatch(ctx)) != S3_OK) return rc;
+    } else if (mode == S3_MINIBATCH) {
+        if (!ctx->mb_graph) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            rc = enqueue_minibatch(ctx);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
+            if (rc != S3_OK) return rc;
+            CK(e);
+            e = cudaGraphInstantiate(&ctx->mb_graph, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(e);
+        }
+        CK(cudaGraphLaunch(ctx->mb_graph, ctx->stream));
+    } else {
+        if ((rc = enqueue_hogwild(ctx)) != S3_OK) return rc;
+    }
+    ctx->epoch += 1;
+    bool bad = false;
+    if ((rc = check_params_finite(ctx, &bad)) != S3_OK) return rc;
+    if (bad) return fail(ctx, S3_ERR_DIVERGED, "non-finite parameter after the epoch");
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ loss / rmse / predict
+extern "C" int s3_loss(s3_ctx* ctx, double* f_out, double* rmse_out) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    const int N = ctx->N, M = ctx->M, nF = N + M;
+    const int tb = tensor_fwd_blocks(ctx->nnz);
+    const int nb_sq = 64;
+    int64_t need = tb;
+    for (int m = 0; m < M; ++m) need = std::max<int64_t>(need, coupled_fwd_blocks(ctx->ynnz[m]));
+    need = std::max<int64_t>(need, (int64_t)(nF + 1) * nb_sq);
+    int rc;
+    if ((rc = ensure_red(ctx, need * 2)) != S3_OK) return rc;
+    float* parts_a = ctx->red_parts;
+    // tensor squared errors over the train entries
+    const int32_t* idx[kMaxN];
+    for (int n = 0; n < N; ++n) idx[n] = ctx->grad.d.tidx[n];
+    CK(prof_mark(ctx, S3_K_TENSOR_FWD));
+    KL(launch_tensor_fwd(N, ctx->JP, ctx->P, idx, ctx->grad.d.tval, ctx->nnz, nullptr, parts_a, ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_FWD));
+    prof_count(ctx, S3_K_TENSOR_FWD, ctx->nnz);
+    KL(launch_reduce_f64(parts_a, tb, ctx->d_red + 0, ctx->stream));
+    for (int m = 0; m < M; ++m) {
+        KL(launch_coupled_fwd(ctx->P, m, ctx->grad.d.cr[m], ctx->grad.d.cc[m], ctx->grad.d.cval[m],
+                              ctx->ynnz[m], parts_a, ctx->stream));
+        KL(launch_reduce_f64(parts_a, coupled_fwd_blocks(ctx->ynnz[m]), ctx->d_red + 1 + m, ctx->stream));
+    }
+    int64_t rows[kMaxF + 1];
+    {
+        size_t q = 1;
+        for (int n = 0; n < N - 1; ++n) q *= ctx->JP;
+        rows[0] = (int64_t)(q * ctx->JPR);
+    }
+    for (int F = 0; F < nF; ++F) rows[F + 1] = factor_rows(ctx, F);
+    KL(launch_sqnorms(ctx->P, nF, rows, ctx->JP, parts_a, nb_sq, ctx->stream));
+    for (int k = 0; k <= nF; ++k)
+        KL(launch_reduce_f64(parts_a + 2 * (int64_t)k * nb_sq, nb_sq, ctx->d_red + 1 + M + k, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double) * (2 + M + nF), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const double* r = ctx->h_red;
+    const double lam = ctx->hp.lambda_reg, lm = ctx->hp.lambda_m;
+    const double se = r[0];
+    double f = 0.5 * se;
+    double regU = r[1 + M + 0];  // ||G||^2
+    for (int n = 0; n < N; ++n) regU += r[1 + M + 1 + n];
+    f += 0.5 * lam * regU;
+    for (int m = 0; m < M; ++m) f += 0.5 * lm * (r[1 + m] + lam * r[1 + M + 1 + N + m]);
+    if (f_out) *f_out = f;
+    if (rmse_out) *rmse_out = sqrt(se / (double)ctx->nnz);
+    if (!std::isfinite(f)) return fail(ctx, S3_ERR_DIVERGED, "non-finite loss");
+    return S3_OK;
+}
+
+// copies test entries to fresh device buffers owned by the caller of this helper
+static int upload_coo(s3_ctx* ctx, const s3_coo_tensor* t, int device_ptrs, int32_t** idx, float** val,
+                      int64_t* n_out) {
+    if (!t || !t->idx || !t->val || t->n_modes != ctx->N || t->nnz < 0)
+        return fail(ctx, S3_ERR_ARG, "invalid test tensor");
+    std::vector<int32_t> h;
+    const size_t n = (size_t)std::max<int64_t>(t->nnz, 1);
+    for (int k = 0; k < ctx->N; ++k) {
+        cudaError_t e = to_host(t->idx[k], t->nnz, device_ptrs, h);
+        if (e != cudaSuccess) return fail(ctx, S3_ERR_ARG, "reading test indices");
+        for (int64_t q = 0; q < t->nnz; ++q)
+            if (h[(size_t)q] < 0 || h[(size_t)q] >= ctx->I[k]) return fail(ctx, S3_ERR_INDEX, "test index out of range");
+        CK(cudaMalloc((void**)&idx[k], n * sizeof(int32_t)));
+        if (t->nnz) CK(cudaMemcpy(idx[k], h.data(), (size_t)t->nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    std::vector<float> v;
+    cudaError_t e = to_host(t->val, t->nnz, device_ptrs, v);
+    if (e != cudaSuccess) return fail(ctx, S3_ERR_ARG, "reading test values");
+    CK(cudaMalloc((void**)val, n * sizeof(float)));
+    if (t->nnz) CK(cudaMemcpy(*val, v.data(), (size_t)t->nnz * sizeof(float), cudaMemcpyHostToDevice));
+    *n_out = t->nnz;
+    return S3_OK;
+}
+
+extern "C" int s3_set_test(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    CK(cudaStreamSynchronize(ctx->stream));
+    int32_t* idx[kMaxN] = {};
+    float* val = nullptr;
+    int64_t n = 0;
+    int rc = upload_coo(ctx, test, device_ptrs, idx, &val, &n);
+    if (rc != S3_OK) {
+        free_coo(idx, &val);
+        return rc;
+    }
+    free_coo(ctx->test_idx, &ctx->test_val);
+    for (int k = 0; k < kMaxN; ++k) ctx->test_idx[k] = idx[k];
+    ctx->test_val = val;
+    ctx->ntest = n;
+    return S3_OK;
+}
+
+extern "C" int s3_rmse(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs, double* rmse_out) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (!rmse_out) return fail(ctx, S3_ERR_ARG, "rmse_out is NULL");
+    const int32_t* idx[kMaxN] = {};
+    const float* val = nullptr;
+    int64_t n = 0;
+    int32_t* tmp_idx[kMaxN] = {};
+    float* tmp_val = nullptr;
+    struct Tmp {
+        int32_t** i;
+        float** v;
+        ~Tmp() { free_coo(i, v); }
+    } tmp{tmp_idx, &tmp_val};
+    if (test) {
+        if (!device_ptrs) {
+            CK(cudaStreamSynchronize(ctx->stream));
+            int rc = upload_coo(ctx, test, 0, tmp_idx, &tmp_val, &n);
+            if (rc != S3_OK) return rc;
+            for (int k = 0; k < ctx->N; ++k) idx[k] = tmp_idx[k];
+            val = tmp_val;
+        } else {
+            if (test->n_modes != ctx->N || !test->idx || !test->val) return fail(ctx, S3_ERR_ARG, "invalid test tensor");
+            for (int k = 0; k < ctx->N; ++k) idx[k] = test->idx[k];
+            val = test->val;
+            n = test->nnz;
+        }
+    } else {
+        for (int k = 0; k < ctx->N; ++k) idx[k] = ctx->test_idx[k];
+        val = ctx->test_val;
+        n = ctx->ntest;
+    }
+    if (n <= 0) { *rmse_out = 0.0; return S3_OK; }
+    const int tb = tensor_fwd_blocks(n);
+    int rc;
+    if ((rc = ensure_red(ctx, tb)) != S3_OK) return rc;
+    CK(prof_mark(ctx, S3_K_TENSOR_FWD));
+    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, val, n, nullptr, ctx->red_parts, ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_FWD));
+    prof_count(ctx, S3_K_TENSOR_FWD, n);
+    KL(launch_reduce_f64(ctx->red_parts, tb, ctx->d_red, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    *rmse_out = sqrt(ctx->h_red[0] / (double)n);
+    return S3_OK;
+}
+
+extern "C" int s3_predict(s3_ctx* ctx, const int32_t* const* idx, int64_t n, float* out) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (n < 0 || (n > 0 && (!idx || !out))) return fail(ctx, S3_ERR_ARG, "invalid predict arguments");
+    if (n == 0) return S3_OK;
+    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, nullptr, n, out, nullptr, ctx->stream));
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ gradient
+extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* const* dV) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    const int N = ctx->N, M = ctx->M, nF = N + M;
+    if (!dG || !dU || (M > 0 && !dV)) return fail(ctx, S3_ERR_ARG, "gradient outputs missing");
+    int64_t pd = 1;
+    for (int n = 0; n < N; ++n) pd *= ctx->J[n];
+    // compensation buffers: core then every factor, unpadded
+    int64_t need = pd;
+    int64_t off[kMaxF];
+    for (int F = 0; F < nF; ++F) { off[F] = need; need += factor_rows(ctx, F) * factor_cols(ctx, F); }
+    if (need > ctx->grad_comp_n) {
+        CK(dalloc(ctx, &ctx->grad_comp, (size_t)need));
+        ctx->grad_comp_n = need;
+    }
+    CK(cudaMemsetAsync(ctx->grad_comp, 0, (size_t)need * sizeof(float), ctx->stream));
+    CK(cudaMemsetAsync(dG, 0, (size_t)pd * sizeof(float), ctx->stream));
+    float* outs[kMaxF];
+    for (int F = 0; F < nF; ++F) {
+        outs[F] = F < N ? dU[F] : dV[F - N];
+        if (!outs[F]) return fail(ctx, S3_ERR_ARG, "gradient output missing");
+        CK(cudaMemsetAsync(outs[F], 0, (size_t)(factor_rows(ctx, F) * factor_cols(ctx, F)) * sizeof(float), ctx->stream));
+    }
+    DevGrouping& D = ctx->grad;
+    for (int64_t g = 0; g < D.ngroups; ++g) {
+        TensorLaunch L{};
+        L.e_begin = D.t_off[(size_t)g];
+        L.e_end = D.t_off[(size_t)g + 1];
+        for (int n = 0; n < N; ++n) L.contrib[n] = ctx->contrib[n];
+        L.core_part = ctx->core_part;
+        CK(prof_mark(ctx, S3_K_TENSOR_GRAD));
+        KL(launch_tensor_contrib(N, ctx->JP, ctx->P, D.d, L, ctx->stream));
+        CK(prof_mark(ctx, S3_K_TENSOR_GRAD));
+        prof_count(ctx, S3_K_TENSOR_GRAD, L.e_end - L.e_begin);
+        for (int m = 0; m < M; ++m)
+            KL(launch_coupled_contrib(ctx->P, D.d, m, D.c_off[m][(size_t)g], D.c_off[m][(size_t)g + 1],
+                                      ctx->contrib[ctx->cmode[m]], ctx->contrib[N + m], ctx->stream));
+        SegmentLaunch S{};
+        S.nF = nF;
+        S.g = g;
+        for (int F = 0; F < nF; ++F) {
+            S.contrib[F] = ctx->contrib[F];
+            S.out[F] = outs[F];
+            S.comp[F] = ctx->grad_comp + off[F];
+            S.Jf[F] = factor_cols(ctx, F);
+            S.seg_begin[F + 1] = S.seg_begin[F] + (D.seg_off[F][(size_t)g + 1] - D.seg_off[F][(size_t)g]);
+        }
+        S.total_segs = S.seg_begin[nF];
+        KL(launch_segments(ctx->P, D.d, S, ctx->d_eta, 0, 1, ctx->stream));
+        const int64_t nt = L.e_end - L.e_begin;
+        KL(launch_core(ctx->P, N, ctx->JP, ctx->J, ctx->core_part, (nt + kTile - 1) / kTile, nt,
+                       ctx->d_eta, 1.f, 1, dG, ctx->grad_comp, ctx->stream));
+    }
+    KL(launch_add_comp(dG, ctx->grad_comp, pd, ctx->stream));
+    for (int F = 0; F < nF; ++F)
+        KL(launch_add_comp(outs[F], ctx->grad_comp + off[F], factor_rows(ctx, F) * factor_cols(ctx, F), ctx->stream));
+    KL(launch_core_reg(dG, ctx->P.G, N, ctx->J, ctx->JP, ctx->hp.lambda_reg, ctx->stream));
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ params
+extern "C" int s3_get_params(s3_ctx* ctx, float* G, float* const* U, float* const* V) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (G) KL(launch_unpack_core(G, ctx->P.G, ctx->N, ctx->J, ctx->JP, ctx->stream));
+    for (int n = 0; n < ctx->N; ++n)
+        if (U && U[n]) KL(launch_unpack_rows(U[n], ctx->P.U[n], ctx->JPR, ctx->I[n], ctx->J[n], ctx->stream));
+    for (int m = 0; m < ctx->M; ++m)
+        if (V && V[m]) KL(launch_unpack_rows(V[m], ctx->P.V[m], ctx->JPR, ctx->K[m], ctx->J[ctx->cmode[m]], ctx->stream));
+    return S3_OK;
+}
+
+extern "C" int s3_set_params(s3_ctx* ctx, const float* G, const float* const* U, const float* const* V) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (G) KL(launch_pack_core(ctx->P.G, G, ctx->N, ctx->J, ctx->JP, ctx->stream));
+    for (int n = 0; n < ctx->N; ++n)
+        if (U && U[n]) KL(launch_pack_rows(ctx->P.U[n], ctx->JPR, U[n], ctx->I[n], ctx->J[n], ctx->stream));
+    for (int m = 0; m < ctx->M; ++m)
+        if (V && V[m]) KL(launch_pack_rows(ctx->P.V[m], ctx->JPR, V[m], ctx->K[m], ctx->J[ctx->cmode[m]], ctx->stream));
+    return S3_OK;
+}
+
+extern "C" int s3_get_epoch(s3_ctx* ctx, int64_t* t) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (!t) return fail(ctx, S3_ERR_ARG, "t is NULL");
+    *t = ctx->epoch;
+    return S3_OK;
+}
+
+extern "C" int s3_set_epoch(s3_ctx* ctx, int64_t t) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (t < 0) return fail(ctx, S3_ERR_ARG, "negative epoch");
+    ctx->epoch = t;
+    return S3_OK;
+}
+
+extern "C" int s3_info(s3_ctx* ctx, int64_t* n_union, int64_t* n_batches, int64_t* n_tiles) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (n_union) *n_union = ctx->n_union;
+    if (n_batches) *n_batches = ctx->mb.ngroups;
+    if (n_tiles) *n_tiles = ctx->hog.ngroups;
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ values from the host
+extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (!x_val) return fail(ctx, S3_ERR_ARG, "x_val is NULL");
+    int64_t total = ctx->nnz;
+    for (int m = 0; m < ctx->M; ++m) total += ctx->ynnz[m];
+    if (!ctx->values_stage) CK(dalloc(ctx, &ctx->values_stage, (size_t)total));
+    CK(cudaMemcpyAsync(ctx->values_stage, x_val, (size_t)ctx->nnz * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    DevGrouping* gs[3] = {&ctx->mb, &ctx->hog, &ctx->grad};
+    for (DevGrouping* D : gs)
+        KL(launch_gather_f32(D->tval, ctx->values_stage, D->t_src, D->t_off.back(), ctx->stream));
+    int64_t o = ctx->nnz;
+    for (int m = 0; m < ctx->M; ++m) {
+        if (y_val && y_val[m]) {
+            CK(cudaMemcpyAsync(ctx->values_stage + o, y_val[m], (size_t)ctx->ynnz[m] * sizeof(float),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            for (DevGrouping* D : gs)
+                KL(launch_gather_f32(D->cval[m], ctx->values_stage + o, D->c_src[m], ctx->ynnz[m], ctx->stream));
+        }
+        o += ctx->ynnz[m];
+    }
+    return S3_OK;
+}

@@ -1,0 +1,83 @@
+// Shared device-side definitions of the S3CMTF sm_103a path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace s3 {
+
+constexpr int kMaxN = 4;               // tensor order supported by the kernels: 3 or 4
+constexpr int kMaxM = 8;               // coupled matrices
+constexpr int kMaxF = kMaxN + kMaxM;   // factor matrices: U^(1..N), then V_1..V_M
+constexpr int kTile = 256;             // tensor entries per CTA tile (one per thread)
+
+// Parameters and per-row constants, all device pointers.  Every factor matrix is stored
+// row-major with row stride `ld` floats (J padded to a multiple of 4, zero padding); the
+// core is stored padded to JP in every mode with the last mode's rows padded to `ldg`.
+struct DParams {
+    float* G;
+    float* U[kMaxN];
+    float* V[kMaxM];
+    const float* inv_cnt[kMaxF];   // 1/|Omega^{n,i}| for factor n, 1/|Omega_Y^{2,k}| for
+                                   // factor N+m; 0 for rows without observed entries
+    int ld;                        // row stride (floats) of every factor matrix
+    int ldg;                       // row stride (floats) of the padded core's last mode
+    int N, M;
+    int cmode[kMaxM];
+    float lambda_reg, lambda_m, inv_nnz;
+};
+
+// One grouping of the items (minibatches, HOGWILD tiles or gradient chunks), device arrays.
+// Tensor entries and coupled entries are stored in group order.  For every factor F each
+// group's occurrences ("events") of rows are sorted by row into segments; `tpos`/`cpos_*`
+// give an event's local slot (position among the group's sorted events of that factor) or
+// local segment, depending on the grouping's kind.
+struct DGroup {
+    const int64_t* t_off;
+    const int32_t* tidx[kMaxN];
+    const float* tval;
+    const int32_t* tpos[kMaxN];
+    const int64_t* c_off[kMaxM];
+    const int32_t* cr[kMaxM];
+    const int32_t* cc[kMaxM];
+    const float* cval[kMaxM];
+    const int32_t* cpos_u[kMaxM];
+    const int32_t* cpos_v[kMaxM];
+    const int64_t* seg_off[kMaxF];     // [groups + 1] global segment range of each group
+    const int32_t* seg_row[kMaxF];     // row of each segment
+    const int32_t* seg_start[kMaxF];   // local slot of the segment's first event
+    const int32_t* seg_cnt[kMaxF];     // events in the segment
+    const int64_t* slot_off[kMaxF];    // [groups + 1] global slot range of each group
+};
+
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
+
+__device__ __forceinline__ float4 ld4_nc(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ld4_cg(const float* p) {
+    return __ldcg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ void st4(float* p, float4 v) {
+    *reinterpret_cast<float4*>(p) = v;
+}
+
+// Vector atomic add of 4 consecutive floats (16-byte aligned) in global memory.
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
+                 :: "l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// Neumaier-compensated FP32 accumulation.
+struct Kahan {
+    float s, c;
+    __device__ __forceinline__ void init() { s = 0.f; c = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        float t = s + x;
+        if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return s + c; }
+};
+
+}  // namespace s3

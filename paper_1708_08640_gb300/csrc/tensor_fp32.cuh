@@ -1,0 +1,276 @@
+// FP32 (CUDA-core) per-tensor-entry arithmetic of S3CMTF, templated on the order N and
+// the padded rank JP.  Shared by the minibatch/gradient, HOGWILD and forward kernels.
+//
+// For an entry alpha = (i_1..i_N) with rows a_n = u^(n)_{i_n} the kernels need
+//   x~    = G x {a}                    (Eq. (4))
+//   p_n   = G x_{-n} {a}, n = 1..N      (the partial products of Eq. (8), Eq. (3))
+//   e a_1 o a_2 o ... o a_N            (the data part of the core gradient, Eq. (8))
+// S3CMTF-opt (Section 3.5, Alg. 3) gets the partials from the intermediate data S by
+// Collapse and element-wise division.  Here they come from one sweep over the core that
+// reuses the contraction with the last mode's row: T = G x_N a_N gives p_n (n < N) by
+// contracting T with the other rows, and the same core values weighted by the products of
+// the first N-1 rows give p_N.  No division, so zero rows are harmless.
+#pragma once
+#include "common.cuh"
+
+namespace s3 {
+
+template <int B, int E>
+struct ipow_t { static constexpr int v = B * ipow_t<B, E - 1>::v; };
+template <int B>
+struct ipow_t<B, 0> { static constexpr int v = 1; };
+
+// loads JP values of a row (stride JPR, 16-byte aligned) into registers
+template <int JP, bool kCoherent>
+__device__ __forceinline__ void load_row(const float* __restrict__ p, float (&a)[JP]) {
+    constexpr int JPR = round4(JP);
+    float t[JPR];
+#pragma unroll
+    for (int q = 0; q < JPR / 4; ++q) {
+        float4 v = kCoherent ? ld4_cg(p + 4 * q) : ld4_nc(p + 4 * q);
+        t[4 * q + 0] = v.x;
+        t[4 * q + 1] = v.y;
+        t[4 * q + 2] = v.z;
+        t[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < JP; ++j) a[j] = t[j];
+}
+
+// one core row (the last mode) from shared memory
+template <int JP>
+__device__ __forceinline__ void load_grow(const float* __restrict__ g, float (&r)[JP]) {
+    constexpr int JPR = round4(JP);
+    float t[JPR];
+#pragma unroll
+    for (int q = 0; q < JPR / 4; ++q) {
+        float4 v = *reinterpret_cast<const float4*>(g + 4 * q);
+        t[4 * q + 0] = v.x;
+        t[4 * q + 1] = v.y;
+        t[4 * q + 2] = v.z;
+        t[4 * q + 3] = v.w;
+    }
+#pragma unroll
+    for (int j = 0; j < JP; ++j) r[j] = t[j];
+}
+
+// ---------------------------------------------------------------- N = 3
+// Returns x~; fills p1, p2, p3.  sG: core in shared memory, [JP][JP][JPR].
+template <int JP>
+__device__ __forceinline__ float partials3(const float* __restrict__ sG, const float (&a1)[JP],
+                                           const float (&a2)[JP], const float (&a3)[JP],
+                                           float (&p1)[JP], float (&p2)[JP], float (&p3)[JP]) {
+    constexpr int JPR = round4(JP);
+    constexpr int U1 = JP <= 12 ? JP : 1;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) { p1[j] = 0.f; p2[j] = 0.f; p3[j] = 0.f; }
+#pragma unroll U1
+    for (int j1 = 0; j1 < JP; ++j1) {
+        const float a1j = a1[j1];
+        float p1j = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < JP; ++j2) {
+            float g[JP];
+            load_grow<JP>(sG + (j1 * JP + j2) * JPR, g);
+            const float w = a1j * a2[j2];
+            float t = 0.f;
+#pragma unroll
+            for (int j3 = 0; j3 < JP; ++j3) {
+                t = fmaf(g[j3], a3[j3], t);
+                p3[j3] = fmaf(g[j3], w, p3[j3]);
+            }
+            p1j = fmaf(t, a2[j2], p1j);
+            p2[j2] = fmaf(t, a1j, p2[j2]);
+        }
+        p1[j1] = p1j;
+    }
+    float xt = 0.f;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) xt = fmaf(a1[j], p1[j], xt);
+    return xt;
+}
+
+// prediction only: x~ = sum_j1 a1 sum_j2 a2 sum_j3 g a3
+template <int JP>
+__device__ __forceinline__ float predict3(const float* __restrict__ sG, const float (&a1)[JP],
+                                          const float (&a2)[JP], const float (&a3)[JP]) {
+    constexpr int JPR = round4(JP);
+    constexpr int U1 = JP <= 12 ? JP : 1;
+    float xt = 0.f;
+#pragma unroll U1
+    for (int j1 = 0; j1 < JP; ++j1) {
+        float s = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < JP; ++j2) {
+            float g[JP];
+            load_grow<JP>(sG + (j1 * JP + j2) * JPR, g);
+            float t = 0.f;
+#pragma unroll
+            for (int j3 = 0; j3 < JP; ++j3) t = fmaf(g[j3], a3[j3], t);
+            s = fmaf(t, a2[j2], s);
+        }
+        xt = fmaf(s, a1[j1], xt);
+    }
+    return xt;
+}
+
+// ---------------------------------------------------------------- N = 4
+template <int JP>
+__device__ __forceinline__ float partials4(const float* __restrict__ sG, const float (&a1)[JP],
+                                           const float (&a2)[JP], const float (&a3)[JP],
+                                           const float (&a4)[JP], float (&p1)[JP],
+                                           float (&p2)[JP], float (&p3)[JP], float (&p4)[JP]) {
+    constexpr int JPR = round4(JP);
+    constexpr int U1 = JP <= 4 ? JP : 1;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) { p1[j] = 0.f; p2[j] = 0.f; p3[j] = 0.f; p4[j] = 0.f; }
+#pragma unroll U1
+    for (int j1 = 0; j1 < JP; ++j1) {
+        const float a1j = a1[j1];
+        float p1j = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < JP; ++j2) {
+            const float w12 = a1j * a2[j2];
+#pragma unroll
+            for (int j3 = 0; j3 < JP; ++j3) {
+                float g[JP];
+                load_grow<JP>(sG + ((j1 * JP + j2) * JP + j3) * JPR, g);
+                const float w = w12 * a3[j3];
+                float t = 0.f;
+#pragma unroll
+                for (int j4 = 0; j4 < JP; ++j4) {
+                    t = fmaf(g[j4], a4[j4], t);
+                    p4[j4] = fmaf(g[j4], w, p4[j4]);
+                }
+                p3[j3] = fmaf(t, w12, p3[j3]);
+                p1j = fmaf(t, a2[j2] * a3[j3], p1j);
+                p2[j2] = fmaf(t, a1j * a3[j3], p2[j2]);
+            }
+        }
+        p1[j1] = p1j;
+    }
+    float xt = 0.f;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) xt = fmaf(a1[j], p1[j], xt);
+    return xt;
+}
+
+template <int JP>
+__device__ __forceinline__ float predict4(const float* __restrict__ sG, const float (&a1)[JP],
+                                          const float (&a2)[JP], const float (&a3)[JP],
+                                          const float (&a4)[JP]) {
+    constexpr int JPR = round4(JP);
+    constexpr int U1 = JP <= 4 ? JP : 1;
+    float xt = 0.f;
+#pragma unroll U1
+    for (int j1 = 0; j1 < JP; ++j1) {
+        float s1 = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < JP; ++j2) {
+            float s2 = 0.f;
+#pragma unroll
+            for (int j3 = 0; j3 < JP; ++j3) {
+                float g[JP];
+                load_grow<JP>(sG + ((j1 * JP + j2) * JP + j3) * JPR, g);
+                float t = 0.f;
+#pragma unroll
+                for (int j4 = 0; j4 < JP; ++j4) t = fmaf(g[j4], a4[j4], t);
+                s2 = fmaf(t, a3[j3], s2);
+            }
+            s1 = fmaf(s2, a2[j2], s1);
+        }
+        xt = fmaf(s1, a1[j1], xt);
+    }
+    return xt;
+}
+
+// ---------------------------------------------------------------- core-gradient accumulator
+// Accumulates sum_b e_b a1_b o ... o aN_b over the entries of a CTA.  The N staged rows of
+// each entry sit in shared memory: stage[n][b][JPR] (stage[0] already multiplied by e_b).
+// Thread t owns multi-indices q over the first N-1 modes and all JP values of the last
+// mode; when there are fewer multi-indices than threads the entries are split into KS
+// slices.  Running sums are Neumaier-compensated across tiles.
+template <int N, int JP>
+struct CoreAcc {
+    static constexpr int JPR = round4(JP);
+    static constexpr int Q = ipow_t<JP, N - 1>::v;
+    static constexpr int KS = (kTile / Q) > 0 ? (kTile / Q) : 1;
+    static constexpr int QPT = (Q + kTile - 1) / kTile;
+    float s[QPT][JP];
+    float c[QPT][JP];
+
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < QPT; ++k)
+#pragma unroll
+            for (int j = 0; j < JP; ++j) { s[k][j] = 0.f; c[k][j] = 0.f; }
+    }
+
+    // stage: shared memory [N][kTile][JPR]; nb valid entries
+    __device__ __forceinline__ void add_tile(const float* __restrict__ stage, int nb) {
+        const int t = threadIdx.x;
+        const int slice = KS > 1 ? t / Q : 0;
+#pragma unroll
+        for (int k = 0; k < QPT; ++k) {
+            const int q = KS > 1 ? (t % Q) : (t + k * kTile);
+            if (slice >= KS || q >= Q) continue;
+            int jj[N - 1];
+            {
+                int r = q;
+#pragma unroll
+                for (int n = N - 2; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
+            }
+            float tile[JP];
+#pragma unroll
+            for (int j = 0; j < JP; ++j) tile[j] = 0.f;
+            for (int b = slice; b < nb; b += KS) {
+                float w = stage[(0 * kTile + b) * JPR + jj[0]];
+#pragma unroll
+                for (int n = 1; n < N - 1; ++n) w *= stage[(n * kTile + b) * JPR + jj[n]];
+                float r[JP];
+                load_grow<JP>(stage + ((N - 1) * kTile + b) * JPR, r);
+#pragma unroll
+                for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < JP; ++j) {
+                const float x = tile[j];
+                const float tt = s[k][j] + x;
+                if (fabsf(s[k][j]) >= fabsf(x)) c[k][j] += (s[k][j] - tt) + x;
+                else c[k][j] += (x - tt) + s[k][j];
+                s[k][j] = tt;
+            }
+        }
+    }
+
+    // Writes this CTA's partial (dense [Q][JP]) to out.  scratch: shared memory of at
+    // least KS * Q * JP floats (only used when KS > 1).  Ends with __syncthreads.
+    __device__ __forceinline__ void store(float* __restrict__ out, float* scratch) {
+        const int t = threadIdx.x;
+        if (KS == 1) {
+#pragma unroll
+            for (int k = 0; k < QPT; ++k) {
+                const int q = t + k * kTile;
+                if (q >= Q) continue;
+#pragma unroll
+                for (int j = 0; j < JP; ++j) out[q * JP + j] = s[k][j] + c[k][j];
+            }
+            __syncthreads();
+            return;
+        }
+        const int slice = t / Q, q = t % Q;
+        if (slice < KS) {
+#pragma unroll
+            for (int j = 0; j < JP; ++j) scratch[(slice * Q + q) * JP + j] = s[0][j] + c[0][j];
+        }
+        __syncthreads();
+        for (int l = t; l < Q * JP; l += kTile) {
+            float a = 0.f;
+            for (int sl = 0; sl < KS; ++sl) a += scratch[sl * Q * JP + l];
+            out[l] = a;
+        }
+        __syncthreads();
+    }
+};
+
+}  // namespace s3

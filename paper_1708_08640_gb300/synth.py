@@ -203,7 +203,7 @@ def _cfg0(rng, noise=0.1):
     r, c = _sparse_matrix(rng, 1_000, 100, 50)
     y = np.einsum("ej,ej->e", Up[0][r], W[c]) + rng.normal(0.0, noise, size=r.shape[0])
     cpl = [Coupled(0, 50, r, c, y)]
-    hp = dict(lr0=0.01, mu=0.1, lambda_reg=0.01, lambda_m=1.0)
+    hp = dict(lr0=0.01, mu=0.1, lambda_reg=0.01, lambda_m=10.0, batch=4096, core_scale=1.0)
     rec = ("3-way 100x100x20, 10k unique uniform coordinates, planted core 5x5x5 ~ N(0,1), "
            "factors ~ U(0,1), + N(0,0.1^2), 90/10 split; coupled 100x50 on mode 1, 1k unique "
            "uniform entries = U1 W^T + N(0,0.1^2), W 50x5 ~ U(0,1)")
@@ -216,7 +216,7 @@ def _rating_like(rng, dims, nnz, J, n_cpl, zipf="zipf1.1"):
     tr_i, tr_v, te_i, te_v = _split(rng, coords, v, 0.10)
     r, c, y = _binary_symmetric(rng, n_cpl, dims[0], zipf)
     cpl = [Coupled(0, dims[0], r, c, y)]
-    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=1.0)
+    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=10.0, batch=4096, core_scale=32.0)
     rec = (f"3-way {dims[0]}x{dims[1]}x{dims[2]}, {nnz} unique coordinates, modes 1-2 "
            f"{zipf}, mode 3 uniform; planted rank-(10,10,10) core ~ N(0,1), factors ~ U(0,1), "
            "standardised to mean 3 std 1, + N(0,0.2^2), rounded half-even, clipped to 1..5; "
@@ -246,7 +246,7 @@ def _fourway(rng, dims, nnz, nA, nB):
     rb, cb = _sparse_matrix(rng, nB, dims[1], 1000)
     yb = np.ones(rb.shape[0])
     cpl = [Coupled(0, 200, ra, ca, ya), Coupled(1, 1000, rb, cb, yb)]
-    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=1.0)
+    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=10.0, batch=4096, core_scale=32.0)
     rec = (f"4-way {'x'.join(map(str, dims))}, {nnz} unique Zipf(1.05) coordinates on all "
            "modes, planted rank-(8,8,8,8) + N(0,0.1^2); coupled A on mode 1 (x200) with "
            f"{nA} N(0,1) entries, coupled B binary on mode 2 (x1000) with {nB} entries")
@@ -259,6 +259,10 @@ def _cfg3(rng):
 
 def _cfg3_small(rng):
     return _fourway(rng, (20_000, 10_000, 50, 24), 500_000, 200_000, 20_000)
+
+
+def _cfg3_tiny(rng):
+    return _fourway(rng, (2_000, 1_000, 20, 24), 30_000, 12_000, 1_200)
 
 
 def _scal(rng, I, nnz):
@@ -285,6 +289,7 @@ PRESETS = {
     "cfg2_small_j32": lambda rng: _cfg1_small(rng, (32, 32, 32)),
     "cfg3": _cfg3,
     "cfg3_small": _cfg3_small,
+    "cfg3_tiny": _cfg3_tiny,
 }
 
 
