@@ -41,7 +41,8 @@ class s3_coo_matrix(C.Structure):
 class s3_hparams(C.Structure):
     _fields_ = [("lr0", C.c_float), ("mu", C.c_float), ("lambda_reg", C.c_float),
                 ("lambda_m", C.c_float), ("batch", C.c_int), ("core_scale", C.c_float),
-                ("row_rule", C.c_int), ("hog_tile", C.c_int), ("hog_round", C.c_int64)]
+                ("row_rule", C.c_int), ("hog_tile", C.c_int), ("hog_round", C.c_int64),
+                ("hog_staleness", C.c_float)]
 
 
 class S3Error(RuntimeError):

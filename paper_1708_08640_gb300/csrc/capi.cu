@@ -51,6 +51,8 @@ struct s3_ctx {
     std::vector<void*> allocs;
     DParams P{};
     float* inv_cnt[kMaxF] = {};
+    float* damp[kMaxF] = {};
+    int64_t hog_grid = 1;
     DevGrouping mb, hog, grad;
     float* contrib[kMaxF] = {};
     float* core_part = nullptr;
@@ -392,7 +394,9 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         CK(dalloc(ctx, &ctx->P.G, q * ctx->JPR));
         CK(cudaMemsetAsync(ctx->P.G, 0, q * ctx->JPR * sizeof(float), ctx->stream));
     }
-    // per-row inverse counts from the train entries (|Omega^{n,i}|, |Omega_Y^{2,k}|)
+    // per-row inverse counts from the train entries (|Omega^{n,i}|, |Omega_Y^{2,k}|), and
+    // every row's occurrences per epoch (tensor entries plus coupled entries that touch it)
+    std::vector<std::vector<int64_t>> occ((size_t)nF);
     for (int F = 0; F < nF; ++F) {
         const int64_t rows = factor_rows(ctx, F);
         std::vector<int64_t> cnt((size_t)rows, 0);
@@ -402,7 +406,10 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         for (int64_t i = 0; i < rows; ++i) inv[(size_t)i] = cnt[(size_t)i] ? (float)(1.0 / (double)cnt[(size_t)i]) : 0.f;
         CK(upload(ctx, &ctx->inv_cnt[F], inv));
         CK(cudaStreamSynchronize(ctx->stream));
+        occ[(size_t)F] = cnt;
     }
+    for (int m = 0; m < n_coupled; ++m)
+        for (int64_t b = 0; b < ctx->ynnz[m]; ++b) occ[(size_t)ctx->cmode[m]][(size_t)hyr[m][(size_t)b]]++;
     fill_params(ctx);
     int rc;
     if ((rc = upload_grouping(ctx, hmb, ctx->mb)) != S3_OK) return rc;
@@ -432,6 +439,30 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(tensor_prepare(N, ctx->JP, ctx->hog_smem <= kMaxSmem ? ctx->hog_smem : 0));
     const int64_t round = hp->hog_round > 0 ? hp->hog_round : (int64_t)1 << 16;
     ctx->hog_round_tiles = std::max<int64_t>(1, (round + tile - 1) / tile);
+    // HOGWILD concurrency: CTAs resident at once, each working on one tile of `tile` entries
+    {
+        const int per_sm = ctx->hog_smem <= kMaxSmem
+                               ? std::max(1, tensor_hog_blocks_per_sm(N, ctx->JP, ctx->hog_smem)) : 1;
+        ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>({(int64_t)per_sm * ctx->num_sms,
+                                                                ctx->core_part_n,
+                                                                ctx->hog_round_tiles}));
+        // staleness-aware step: a row with kappa updates expected in flight at once takes
+        // gamma / kappa of its step when kappa > gamma (kappa = occurrences x entries in
+        // flight / |Omega|)
+        const double gamma = hp->hog_staleness == 0.f ? 32.0 : (double)hp->hog_staleness;
+        const double inflight = (double)ctx->hog_grid * (double)tile;
+        for (int F = 0; F < nF; ++F) {
+            std::vector<float> d(occ[(size_t)F].size(), 1.f);
+            if (gamma > 0)
+                for (size_t i = 0; i < d.size(); ++i) {
+                    const double kappa = (double)occ[(size_t)F][i] * inflight / (double)ctx->nnz;
+                    if (kappa > gamma) d[i] = (float)(gamma / kappa);
+                }
+            CK(upload(ctx, &ctx->damp[F], d));
+            ctx->P.damp[F] = ctx->damp[F];
+            CK(cudaStreamSynchronize(ctx->stream));
+        }
+    }
     // initial parameters
     KL(launch_init_params(ctx->P, ctx->I, ctx->J, ctx->K, ctx->JP, seed, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -547,13 +578,10 @@ static int enqueue_hogwild(s3_ctx* ctx) {
         return fail(ctx, S3_ERR_ARG, "a HOGWILD tile needs " + std::to_string(ctx->hog_smem) +
                                          " bytes of shared memory; lower hog_tile");
     const int nF = ctx->N + ctx->M;
-    const size_t smem = tensor_hog_smem(ctx->N, ctx->JP, D.max_seg, nF);
-    const int per_sm = std::max(1, tensor_hog_blocks_per_sm(ctx->N, ctx->JP, smem));
-    const int64_t cap = std::min<int64_t>((int64_t)per_sm * ctx->num_sms, ctx->core_part_n);
     const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
     for (int64_t t0 = 0; t0 < D.ngroups; t0 += ctx->hog_round_tiles) {
         const int64_t t1 = std::min(D.ngroups, t0 + ctx->hog_round_tiles);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t1 - t0, cap));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t1 - t0, ctx->hog_grid));
         const int64_t nt = D.t_off[(size_t)t1] - D.t_off[(size_t)t0];
         CK(prof_mark(ctx, S3_K_TENSOR_HOG));
         KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->P, D.d, t0, t1, grid, ctx->d_eta, row_mean,
@@ -586,16 +614,28 @@ extern "C" int s3_epoch(s3_ctx* ctx, int mode, int precision) {
     if (precision == S3_BF16) return fail(ctx, S3_ERR_ARG, "BF16 form not built for this configuration");
     *ctx->h_eta = eta_of(ctx, ctx->epoch);
     CK(cudaMemcpyAsync(ctx->d_eta, ctx->h_eta, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    int rc;
+    int rc = S3_OK;
     if (mode == S3_MINIBATCH && ctx->prof) {
         if ((rc = enqueue_minibatch(ctx)) != S3_OK) return rc;
     } else if (mode == S3_MINIBATCH) {
         if (!ctx->mb_graph) {
-            cudaGraph_t graph;
-            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            rc = enqueue_minibatch(ctx);
-            cudaError_t e = cudaStreamEndCapture(ctx->stream, &graph);
-            if (rc != S3_OK) return rc;
+            // capture on a private stream (the caller's may be the legacy default stream,
+            // which cannot be captured); the graph is then launched on the caller's stream
+            cudaStream_t user = ctx->stream, cap = nullptr;
+            CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                ctx->stream = cap;
+                rc = enqueue_minibatch(ctx);
+                ctx->stream = user;
+                e = cudaStreamEndCapture(cap, &graph);
+            }
+            cudaStreamDestroy(cap);
+            if (rc != S3_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return rc;
+            }
             CK(e);
             e = cudaGraphInstantiate(&ctx->mb_graph, graph, 0);
             cudaGraphDestroy(graph);

@@ -19,6 +19,7 @@ struct DParams {
     float* V[kMaxM];
     const float* inv_cnt[kMaxF];   // 1/|Omega^{n,i}| for factor n, 1/|Omega_Y^{2,k}| for
                                    // factor N+m; 0 for rows without observed entries
+    const float* damp[kMaxF];      // HOGWILD step scale of each row (staleness-aware)
     int ld;                        // row stride (floats) of every factor matrix
     int ldg;                       // row stride (floats) of the padded core's last mode
     int N, M;

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kTile) k_tensor_hog(DParams P, DGroup Gr, int6
                 const int s = l / (JPR / 4), q = l % (JPR / 4);
                 const int32_t rr = __ldg(Gr.seg_row[F] + sg0 + s);
                 const float den = row_mean ? (float)__ldg(Gr.seg_cnt[F] + sg0 + s) : 1.f;
-                const float sc = -eta / den;
+                const float sc = -eta * __ldg(P.damp[F] + rr) / den;
                 const float4 v = *reinterpret_cast<const float4*>(sa + s * JPR + 4 * q);
                 red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * v.x, sc * v.y, sc * v.z, sc * v.w);
             }

@@ -63,3 +63,19 @@ def assert_close_blocks(got, ref, rtol, floor, what=""):
     bad = np.abs(got - ref) > rtol * np.abs(ref) + floor * scale
     assert not bad.any(), (f"{what}: {int(bad.sum())} elements off, worst "
                            f"{np.abs(got - ref).max():.3e} (scale {scale:.3e})")
+
+
+def assert_step_close(new, ref_new, old, rtol, what=""):
+    """A step computed in FP32 and stored as FP32: the delta new - old may differ from the
+    oracle's by rtol relative plus the storage rounding of the new parameter (half an FP32
+    ulp, 2^-24 |p|, twice for safety), elementwise and in norm."""
+    new = np.asarray(new, dtype=np.float64)
+    ref_new = np.asarray(ref_new, dtype=np.float64)
+    old = np.asarray(old, dtype=np.float64)
+    dg, dr = new - old, ref_new - old
+    store = 2.0 ** -23 * np.abs(ref_new)
+    err = np.abs(dg - dr)
+    assert np.linalg.norm(dg - dr) <= rtol * np.linalg.norm(dr) + np.linalg.norm(store), (
+        f"{what}: norm-wise {np.linalg.norm(dg - dr):.3e} vs |d| {np.linalg.norm(dr):.3e}")
+    bad = err > rtol * np.abs(dr) + store + 1e-6 * (np.abs(dr).max() if dr.size else 0.0)
+    assert not bad.any(), f"{what}: {int(bad.sum())} elements off, worst {err.max():.3e}"
