@@ -197,6 +197,60 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- forms
+def precision_forms(p, order, stream, args, epochs=4):
+    """The FP32 and BF16 forms of the HOGWILD epoch on the same data at J = 16 (the cfg2
+    workload): epoch time, nnz-updates/s, test RMSE per epoch, and the tensor-pass kernel's
+    roofline (FP32 FFMA roof for the FP32 form, BF16 tensor roof for the BF16 form)."""
+    import copy
+    import ctypes as C
+
+    import torch
+
+    from paper_1708_08640_gb300 import _lib as L
+    from paper_1708_08640_gb300.model import S3CMTF
+    q = copy.copy(p)
+    q.J = (16, 16, 16)
+    init = synth.init_params(q, 1)
+    peaks, src = measured_peaks()
+    out = {}
+    for prec in ("fp32", "bf16"):
+        m = S3CMTF.from_problem(q, order=order, stream=stream)
+        m.set_params(*init)
+        m.set_test(q.test_idx, q.test_val)
+        m.epoch("hogwild", prec)
+        m.rmse()
+        L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(epochs):
+            m.epoch("hogwild", prec)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / epochs
+        kms, kn, ke = C.c_double(), C.c_int64(), C.c_int64()
+        L.check(m.lib, m.ctx, m.lib.s3_profile_read(m.ctx, L.S3_K_TENSOR_HOG, C.byref(kms),
+                                                      C.byref(kn), C.byref(ke)))
+        L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 0))
+        flops = 6.0 * 16 ** 3 * ke.value
+        achieved = flops / (kms.value / 1000.0) / 1e12
+        if prec == "fp32":
+            roof = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "peak_source": "derived"}
+        else:
+            roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"],
+                    "peak_source": f"{src} bf16_tflops_sustained"}
+        roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
+                     "kernel_ms_per_epoch": kms.value / epochs, "flops_per_entry": 6.0 * 16 ** 3})
+        out[prec] = {"ms_per_epoch": ms, "nnz_updates_per_s": q.n_union / (ms / 1000.0),
+                     "test_rmse_after": m.rmse(), "epochs": 1 + epochs, "roofline": roof}
+        m.close()
+    out["bf16_speedup"] = out["fp32"]["ms_per_epoch"] / out["bf16"]["ms_per_epoch"]
+    out["rmse_rel_diff"] = (out["bf16"]["test_rmse_after"] - out["fp32"]["test_rmse_after"]) / \
+        out["fp32"]["test_rmse_after"]
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
 def run_ours(args, world, rank, local):
     import ctypes as C
@@ -309,6 +363,7 @@ def run_ours(args, world, rank, local):
             extras["minibatch_epoch"] = {"ms": mb_ms, "nnz_updates_per_s": items / (mb_ms / 1000.0),
                                          "batches": model.info()["n_batches"]}
             m2.close()
+        extras["forms_j16"] = precision_forms(p, order, stream, args)
 
     # ---- end to end through the public API with host buffers
     xv = torch.tensor(p.train_val, dtype=torch.float32).pin_memory()

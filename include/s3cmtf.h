@@ -89,12 +89,13 @@ typedef struct {
     int row_rule;       /* S3_ROW_SUM or S3_ROW_MEAN: a row takes the sum, or the mean, of
                            its gradients within one group (batch or HOGWILD tile) */
     int hog_tile;       /* HOGWILD: tensor entries per tile (0 = default 256) */
-    int64_t hog_round;  /* HOGWILD: tensor entries between core updates (0 = default 65536) */
     float hog_staleness;/* HOGWILD: gamma of the staleness-aware row step.  A row expected to
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by
                            gamma / kappa; every other row takes the plain lock-free step.
                            0 = default 32; < 0 disables the scaling. */
+    int hog_ctas;       /* HOGWILD: CTAs working at once (0 = as many as fit on the GPU).
+                           Fewer CTAs mean fewer stale updates in flight and less throughput. */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.
@@ -130,9 +131,9 @@ int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y, in
  *              visiting order run concurrently, each reading the current rows, combining
  *              its gradients per row (row_rule) and adding the step atomically (rows with
  *              many updates in flight take the staleness-aware step of hp.hog_staleness);
- *              the core is read-only within a round of hp.hog_round tensor entries and then
- *              takes one step with the round's mean core gradient (the GPU counterpart of
- *              the paper's "core updated by one worker"); not deterministic.
+ *              the core is updated lock-free too: each tile adds core_scale / W of the
+ *              core step of its mean gradient (W = tiles in flight), so that one wave of
+ *              tiles moves the core by one group step; not deterministic.
  *   precision  S3_FP32 (CUDA-core FP32), or S3_BF16 (tensor-core contraction with BF16
  *              operands and FP32 accumulation; FP32 master parameters and errors).
  * Returns S3_ERR_DIVERGED if a non-finite parameter appeared (the parameters are left as

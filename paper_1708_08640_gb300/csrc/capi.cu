@@ -65,15 +65,17 @@ struct s3_ctx {
     float* h_eta = nullptr;        // pinned
     int* d_flag = nullptr;
     int* h_flag = nullptr;         // pinned
+    int* d_tile_counter = nullptr; // HOGWILD tile claims
+    int* d_kerr = nullptr;         // set by a kernel whose bounded wait ran out
     float* grad_comp = nullptr;    // compensation buffers of the gradient (all parameters)
     int64_t grad_comp_n = 0;
     float* values_stage = nullptr; // s3_update_values staging (nnz + sum ynnz floats)
     int64_t ntest = 0;
     int32_t* test_idx[kMaxN] = {};
     float* test_val = nullptr;
-    int64_t hog_round_tiles = 0;
     size_t hog_smem = 0;
-    cudaGraphExec_t mb_graph = nullptr;
+    int mb_grid = 0;               // CTAs of the persistent minibatch epoch
+    unsigned* d_bar = nullptr;     // its grid-barrier counter and generation
     // measurement (s3_profile)
     bool prof = false;
     int64_t launches = 0;
@@ -288,7 +290,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     ctx->JPR = round4(ctx->JP);
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
-        hp->hog_tile < 0 || hp->hog_round < 0)
+        hp->hog_tile < 0 || hp->hog_ctas < 0)
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];
@@ -434,18 +436,22 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(dalloc(ctx, &ctx->d_eta, 1));
     CK(cudaMallocHost((void**)&ctx->h_eta, sizeof(float)));
     CK(dalloc(ctx, &ctx->d_flag, 1));
-    CK(cudaMallocHost((void**)&ctx->h_flag, sizeof(int)));
+    CK(dalloc(ctx, &ctx->d_tile_counter, 1));
+    CK(dalloc(ctx, &ctx->d_kerr, 1));
+    CK(dalloc(ctx, &ctx->d_bar, 2));
+    CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+    ctx->mb_grid = std::min<int>(minibatch_epoch_grid(N, ctx->JP, ctx->num_sms), (int)ctx->core_part_n);
+    CK(cudaMemsetAsync(ctx->d_kerr, 0, sizeof(int), ctx->stream));
+    CK(cudaMallocHost((void**)&ctx->h_flag, 2 * sizeof(int)));
     ctx->hog_smem = tensor_hog_smem(N, ctx->JP, ctx->hog.max_seg, nF);
     CK(tensor_prepare(N, ctx->JP, ctx->hog_smem <= kMaxSmem ? ctx->hog_smem : 0));
-    const int64_t round = hp->hog_round > 0 ? hp->hog_round : (int64_t)1 << 16;
-    ctx->hog_round_tiles = std::max<int64_t>(1, (round + tile - 1) / tile);
     // HOGWILD concurrency: CTAs resident at once, each working on one tile of `tile` entries
     {
         const int per_sm = ctx->hog_smem <= kMaxSmem
                                ? std::max(1, tensor_hog_blocks_per_sm(N, ctx->JP, ctx->hog_smem)) : 1;
-        ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>({(int64_t)per_sm * ctx->num_sms,
-                                                                ctx->core_part_n,
-                                                                ctx->hog_round_tiles}));
+        int64_t cap = (int64_t)per_sm * ctx->num_sms;
+        if (hp->hog_ctas > 0) cap = std::min<int64_t>(cap, hp->hog_ctas);
+        ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(cap, ctx->hog.ngroups));
         // staleness-aware step: a row with kappa updates expected in flight at once takes
         // gamma / kappa of its step when kappa > gamma (kappa = occurrences x entries in
         // flight / |Omega|)
@@ -490,7 +496,6 @@ static void prof_clear(s3_ctx* ctx) {
 
 extern "C" void s3_destroy(s3_ctx* ctx) {
     if (!ctx) return;
-    if (ctx->mb_graph) cudaGraphExecDestroy(ctx->mb_graph);
     prof_clear(ctx);
     free_coo(ctx->test_idx, &ctx->test_val);
     cudaStreamSynchronize(ctx->stream);
@@ -539,36 +544,24 @@ extern "C" const char* s3_last_error(const s3_ctx* ctx) {
 
 // ------------------------------------------------------------------ epoch
 static int enqueue_minibatch(s3_ctx* ctx) {
-    const int N = ctx->N, M = ctx->M, nF = N + M;
-    DevGrouping& D = ctx->mb;
-    const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
-    for (int64_t g = 0; g < D.ngroups; ++g) {
-        TensorLaunch L{};
-        L.e_begin = D.t_off[(size_t)g];
-        L.e_end = D.t_off[(size_t)g + 1];
-        for (int n = 0; n < N; ++n) L.contrib[n] = ctx->contrib[n];
-        L.core_part = ctx->core_part;
-        CK(prof_mark(ctx, S3_K_TENSOR_MB));
-        KL(launch_tensor_contrib(N, ctx->JP, ctx->P, D.d, L, ctx->stream));
-        CK(prof_mark(ctx, S3_K_TENSOR_MB));
-        prof_count(ctx, S3_K_TENSOR_MB, L.e_end - L.e_begin);
-        for (int m = 0; m < M; ++m)
-            KL(launch_coupled_contrib(ctx->P, D.d, m, D.c_off[m][(size_t)g], D.c_off[m][(size_t)g + 1],
-                                      ctx->contrib[ctx->cmode[m]], ctx->contrib[N + m], ctx->stream));
-        SegmentLaunch S{};
-        S.nF = nF;
-        S.g = g;
-        S.seg_begin[0] = 0;
-        for (int F = 0; F < nF; ++F) {
-            S.contrib[F] = ctx->contrib[F];
-            S.seg_begin[F + 1] = S.seg_begin[F] + (D.seg_off[F][(size_t)g + 1] - D.seg_off[F][(size_t)g]);
-        }
-        S.total_segs = S.seg_begin[nF];
-        KL(launch_segments(ctx->P, D.d, S, ctx->d_eta, row_mean, 0, ctx->stream));
-        const int64_t nt = L.e_end - L.e_begin;
-        KL(launch_core(ctx->P, N, ctx->JP, ctx->J, ctx->core_part, (nt + kTile - 1) / kTile, nt,
-                       ctx->d_eta, ctx->hp.core_scale, 0, nullptr, nullptr, ctx->stream));
-    }
+    const int nF = ctx->N + ctx->M;
+    if (ctx->mb_grid <= 0) return fail(ctx, S3_ERR_ARG, "the minibatch kernel cannot be made co-resident");
+    MbLaunch L{};
+    for (int F = 0; F < nF; ++F) L.contrib[F] = ctx->contrib[F];
+    L.core_part = ctx->core_part;
+    L.bar_count = ctx->d_bar;
+    L.bar_gen = ctx->d_bar + 1;
+    L.err_flag = ctx->d_kerr;
+    L.eta = ctx->d_eta;
+    L.core_scale = ctx->hp.core_scale;
+    L.row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
+    L.n_batches = ctx->mb.ngroups;
+    L.grid = ctx->mb_grid;
+    CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_MB));
+    KL(launch_minibatch_epoch(ctx->N, ctx->JP, ctx->P, ctx->mb.d, L, ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_MB));
+    prof_count(ctx, S3_K_TENSOR_MB, ctx->nnz);
     return S3_OK;
 }
 
@@ -577,20 +570,37 @@ static int enqueue_hogwild(s3_ctx* ctx) {
     if (ctx->hog_smem > kMaxSmem)
         return fail(ctx, S3_ERR_ARG, "a HOGWILD tile needs " + std::to_string(ctx->hog_smem) +
                                          " bytes of shared memory; lower hog_tile");
-    const int nF = ctx->N + ctx->M;
     const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
-    for (int64_t t0 = 0; t0 < D.ngroups; t0 += ctx->hog_round_tiles) {
-        const int64_t t1 = std::min(D.ngroups, t0 + ctx->hog_round_tiles);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t1 - t0, ctx->hog_grid));
-        const int64_t nt = D.t_off[(size_t)t1] - D.t_off[(size_t)t0];
-        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
-        KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->P, D.d, t0, t1, grid, ctx->d_eta, row_mean,
-                             ctx->core_part, D.max_seg, ctx->stream));
-        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
-        prof_count(ctx, S3_K_TENSOR_HOG, nt);
-        KL(launch_core(ctx->P, ctx->N, ctx->JP, ctx->J, ctx->core_part, grid, nt, ctx->d_eta,
-                       ctx->hp.core_scale, 0, nullptr, nullptr, ctx->stream));
-    }
+    CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+    KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter,
+                         (int)ctx->hog_grid, ctx->d_eta, row_mean,
+                         ctx->hp.core_scale / (float)ctx->hog_grid, D.max_seg, ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+    prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
+    return S3_OK;
+}
+
+static int enqueue_hogwild_bf16(s3_ctx* ctx) {
+    DevGrouping& D = ctx->hog;
+    const int nF = ctx->N + ctx->M;
+    if (ctx->N != 3 || ctx->JP != 16)
+        return fail(ctx, S3_ERR_ARG, "the BF16 form is built for 3-way tensors with ranks 11..16");
+    const size_t smem = tensor_hog_bf16_smem(ctx->JP, D.max_seg, nF);
+    if (smem > kMaxSmem)
+        return fail(ctx, S3_ERR_ARG, "a BF16 HOGWILD tile needs " + std::to_string(smem) +
+                                         " bytes of shared memory; lower hog_tile");
+    const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
+    int64_t cap = ctx->num_sms;   // one CTA per SM (shared memory and TMEM)
+    if (ctx->hp.hog_ctas > 0) cap = std::min<int64_t>(cap, ctx->hp.hog_ctas);
+    const int grid = (int)std::min<int64_t>(cap, D.ngroups);
+    CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+    KL(launch_tensor_hog_bf16(ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
+                              ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid, D.max_seg,
+                              ctx->d_kerr, ctx->stream));
+    CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+    prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
     return S3_OK;
 }
 
@@ -602,7 +612,12 @@ static int check_params_finite(s3_ctx* ctx, bool* bad) {
     for (int F = 0; F < ctx->N + ctx->M; ++F)
         KL(launch_check_finite(factor_ptr(ctx, F), factor_rows(ctx, F) * ctx->JPR, ctx->d_flag, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_flag + 1, ctx->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->h_flag[1]) {
+        ctx->failed = true;
+        return fail(ctx, S3_ERR_CUDA, "a tensor-core wait timed out in the epoch kernel");
+    }
     *bad = *ctx->h_flag != 0;
     return S3_OK;
 }
@@ -611,37 +626,15 @@ extern "C" int s3_epoch(s3_ctx* ctx, int mode, int precision) {
     if (!usable(ctx)) return S3_ERR_STATE;
     if (mode != S3_MINIBATCH && mode != S3_HOGWILD) return fail(ctx, S3_ERR_ARG, "unknown mode");
     if (precision != S3_FP32 && precision != S3_BF16) return fail(ctx, S3_ERR_ARG, "unknown precision");
-    if (precision == S3_BF16) return fail(ctx, S3_ERR_ARG, "BF16 form not built for this configuration");
+    if (precision == S3_BF16 && mode != S3_HOGWILD)
+        return fail(ctx, S3_ERR_ARG, "the BF16 form is built for the HOGWILD epoch");
     *ctx->h_eta = eta_of(ctx, ctx->epoch);
     CK(cudaMemcpyAsync(ctx->d_eta, ctx->h_eta, sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     int rc = S3_OK;
-    if (mode == S3_MINIBATCH && ctx->prof) {
+    if (mode == S3_MINIBATCH) {
         if ((rc = enqueue_minibatch(ctx)) != S3_OK) return rc;
-    } else if (mode == S3_MINIBATCH) {
-        if (!ctx->mb_graph) {
-            // capture on a private stream (the caller's may be the legacy default stream,
-            // which cannot be captured); the graph is then launched on the caller's stream
-            cudaStream_t user = ctx->stream, cap = nullptr;
-            CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-            cudaGraph_t graph = nullptr;
-            cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
-            if (e == cudaSuccess) {
-                ctx->stream = cap;
-                rc = enqueue_minibatch(ctx);
-                ctx->stream = user;
-                e = cudaStreamEndCapture(cap, &graph);
-            }
-            cudaStreamDestroy(cap);
-            if (rc != S3_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return rc;
-            }
-            CK(e);
-            e = cudaGraphInstantiate(&ctx->mb_graph, graph, 0);
-            cudaGraphDestroy(graph);
-            CK(e);
-        }
-        CK(cudaGraphLaunch(ctx->mb_graph, ctx->stream));
+    } else if (precision == S3_BF16) {
+        if ((rc = enqueue_hogwild_bf16(ctx)) != S3_OK) return rc;
     } else {
         if ((rc = enqueue_hogwild(ctx)) != S3_OK) return rc;
     }

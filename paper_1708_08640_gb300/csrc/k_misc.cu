@@ -215,6 +215,8 @@ cudaError_t launch_segments(const DParams& P, const DGroup& G, const SegmentLaun
 
 // ------------------------------------------------------------------ core step
 // parts: nparts partials, each dense [JP^N] (last mode fastest); G: padded [JP^(N-1)][JPR].
+// One warp per core element: the lanes stride over the partials with compensated sums and
+// combine them with a fixed xor butterfly (deterministic).
 __global__ void __launch_bounds__(256) k_core(DParams P, int N, int JP, int4 Jv,
                                               const float* parts, int64_t nparts, int64_t n_t,
                                               const float* eta_p, float cs, int mode, float* out,
@@ -223,12 +225,16 @@ __global__ void __launch_bounds__(256) k_core(DParams P, int N, int JP, int4 Jv,
     for (int n = 0; n < N; ++n) Pd *= JP;
     const int JPR = round4(JP);
     const int Jn[4] = {Jv.x, Jv.y, Jv.z, Jv.w};
-    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < Pd;
-         l += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < Pd; l += nwarps) {
         Kahan k;
         k.init();
-        for (int64_t p = 0; p < nparts; ++p) k.add(__ldcg(parts + p * Pd + l));
-        const float sum = k.value();
+        for (int64_t p = lane; p < nparts; p += 32) k.add(__ldcg(parts + p * Pd + l));
+        float sum = k.value();
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane != 0) continue;
         const int64_t q = l / JP;
         const int jl = (int)(l % JP);
         if (mode == 0) {
@@ -264,7 +270,7 @@ cudaError_t launch_core(const DParams& P, int N, int JP, const int* J, const flo
                         float* out, float* comp, cudaStream_t s) {
     int64_t Pd = 1;
     for (int n = 0; n < N; ++n) Pd *= JP;
-    const unsigned grid = (unsigned)std::min<int64_t>((Pd + 255) / 256, 1024);
+    const unsigned grid = (unsigned)std::min<int64_t>((Pd * 32 + 255) / 256, 4096);
     int4 Jv = make_int4(J[0], N > 1 ? J[1] : 1, N > 2 ? J[2] : 1, N > 3 ? J[3] : 1);
     k_core<<<grid, 256, 0, s>>>(P, N, JP, Jv, parts, nparts, n_t, eta, core_scale, mode, out, comp);
     return cudaGetLastError();

@@ -14,18 +14,13 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "hog_common.cuh"
 #include "tensor_fp32.cuh"
 
 namespace s3 {
 
 struct IdxPtrs {
     const int32_t* p[kMaxN];
-};
-
-// per-factor offsets (floats) of the HOGWILD row accumulators in shared memory
-struct HogSmem {
-    int off[kMaxF];
-    int nF;
 };
 
 template <int N, int JP>
@@ -96,28 +91,31 @@ __global__ void __launch_bounds__(kTile) k_tensor_contrib(DParams P, DGroup Gr, 
 }
 
 // ------------------------------------------------------------------ HOGWILD
+// One persistent launch per epoch.  CTAs claim tiles in visiting order from a global
+// counter; a tile reads the current rows and core (coherent loads: other CTAs update them
+// concurrently), combines its row gradients in shared memory, adds the row steps with vector
+// atomics and adds its share of the core step to G (lock-free, like the rows).
 template <int N, int JP>
-__global__ void __launch_bounds__(kTile) k_tensor_hog(DParams P, DGroup Gr, int64_t t_begin,
-                                                      int64_t t_end, const float* eta_p,
-                                                      int row_mean, float* core_part,
+__global__ void __launch_bounds__(kTile) k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
+                                                      int* tile_counter, const float* eta_p,
+                                                      int row_mean, float core_step_scale,
                                                       HogSmem H) {
     constexpr int JPR = round4(JP);
     constexpr int Q = ipow_t<JP, N - 1>::v;
     extern __shared__ __align__(16) float smem[];
+    __shared__ int s_tile;
     float* sG = smem;
     float* stage = smem + Q * JPR;
     const float eta = *eta_p;
     const int tid = threadIdx.x;
-    load_core_smem<N, JP>(sG, P.G);
-    CoreAcc<N, JP> acc;
-    acc.init();
-    for (int64_t t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
-        // clear this tile's row accumulators
-        for (int F = 0; F < H.nF; ++F) {
-            const int nseg = (int)(Gr.seg_off[F][t + 1] - Gr.seg_off[F][t]);
-            float* sa = smem + H.off[F];
-            for (int l = tid * 4; l < nseg * JPR; l += kTile * 4) st4(sa + l, make_float4(0, 0, 0, 0));
-        }
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+        // current core (coherent: other CTAs add to it)
+        for (int l = tid * 4; l < Q * JPR; l += kTile * 4) st4(sG + l, ld4_cg(P.G + l));
+        __syncthreads();
+        const int64_t t = s_tile;
+        if (t >= n_tiles) break;
+        hog_clear<JPR>(smem, Gr, t, H);
         __syncthreads();
         const int64_t e0 = Gr.t_off[t];
         const int nb = (int)(Gr.t_off[t + 1] - e0);
@@ -143,50 +141,18 @@ __global__ void __launch_bounds__(kTile) k_tensor_hog(DParams P, DGroup Gr, int6
                 for (int j = 0; j < JP; ++j) sp[j] = n == 0 ? err * a[n][j] : a[n][j];
             }
         }
-        // coupled entries of the tile
-        for (int m = 0; m < P.M; ++m) {
-            const int c = P.cmode[m];
-            const int64_t c0 = Gr.c_off[m][t], c1 = Gr.c_off[m][t + 1];
-            const float lm = P.lambda_m;
-            for (int64_t e = c0 + tid; e < c1; e += kTile) {
-                const int32_t r = __ldg(Gr.cr[m] + e), k = __ldg(Gr.cc[m] + e);
-                float u[JP], v[JP];
-                load_row<JP, true>(P.U[c] + (int64_t)r * JPR, u);
-                load_row<JP, true>(P.V[m] + (int64_t)k * JPR, v);
-                float yh = 0.f;
-#pragma unroll
-                for (int j = 0; j < JP; ++j) yh = fmaf(u[j], v[j], yh);
-                const float err = __ldg(Gr.cval[m] + e) - yh;
-                const float rv = lm * P.lambda_reg * __ldg(P.inv_cnt[P.N + m] + k);
-                float* su = smem + H.off[c] + __ldg(Gr.cpos_u[m] + e) * JPR;
-                float* sv = smem + H.off[P.N + m] + __ldg(Gr.cpos_v[m] + e) * JPR;
-#pragma unroll
-                for (int j = 0; j < JP; ++j) {
-                    atomicAdd(su + j, -lm * err * v[j]);
-                    atomicAdd(sv + j, fmaf(-lm * err, u[j], rv * v[j]));
-                }
-            }
-        }
+        hog_coupled<JP>(P, Gr, t, smem, H);
         __syncthreads();
-        acc.add_tile(stage, nb);
-        // apply this tile's steps: one vector atomic per 4 values of every touched row
-        for (int F = 0; F < H.nF; ++F) {
-            const int64_t sg0 = Gr.seg_off[F][t];
-            const int nseg = (int)(Gr.seg_off[F][t + 1] - sg0);
-            const float* sa = smem + H.off[F];
-            float* base = F < P.N ? P.U[F] : P.V[F - P.N];
-            for (int l = tid; l < nseg * (JPR / 4); l += kTile) {
-                const int s = l / (JPR / 4), q = l % (JPR / 4);
-                const int32_t rr = __ldg(Gr.seg_row[F] + sg0 + s);
-                const float den = row_mean ? (float)__ldg(Gr.seg_cnt[F] + sg0 + s) : 1.f;
-                const float sc = -eta * __ldg(P.damp[F] + rr) / den;
-                const float4 v = *reinterpret_cast<const float4*>(sa + s * JPR + 4 * q);
-                red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * v.x, sc * v.y, sc * v.z, sc * v.w);
-            }
+        // core: this tile's share of the core step,
+        //   G += eta * cs / W * (sum_b e_b a1 o..o aN / n_t - lambda_reg / |Omega| * G)
+        if (nb > 0) {
+            const float sc = eta * core_step_scale / (float)nb;
+            const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
+            CoreTile<N, JP>::apply(stage, nb, sG, P.G, sc, rg);
         }
+        hog_flush<JPR>(P, Gr, t, smem, H, eta, row_mean);
         __syncthreads();
     }
-    acc.store(core_part + (int64_t)blockIdx.x * (Q * JP), stage);
 }
 
 // ------------------------------------------------------------------ forward
@@ -268,9 +234,11 @@ size_t tensor_hog_smem(int N, int JP, const int64_t* max_segs, int nF) {
     return b * sizeof(float);
 }
 
+// the opt-in above 48 KB counts static shared memory too, so set the limit whenever the
+// dynamic part is large
 template <typename K>
 static cudaError_t prep(K kernel, size_t smem) {
-    if (smem > 48 * 1024)
+    if (smem > 32 * 1024)
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return cudaSuccess;
 }
@@ -293,11 +261,10 @@ cudaError_t launch_tensor_contrib(int N, int JP, const DParams& P, const DGroup&
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G,
-                               int64_t t_begin, int64_t t_end, int grid, const float* eta,
-                               int row_mean, float* core_part, const int64_t* max_segs,
-                               cudaStream_t s) {
-    if (t_end <= t_begin) return cudaSuccess;
+cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
+                              int* tile_counter, int grid, const float* eta, int row_mean,
+                              float core_step_scale, const int64_t* max_segs, cudaStream_t s) {
+    if (n_tiles <= 0) return cudaSuccess;
     HogSmem H;
     H.nF = P.N + P.M;
     size_t off = tensor_contrib_smem(N, JP) / sizeof(float);
@@ -310,8 +277,8 @@ cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G,
     if (N == NN && JP == JJ) {                                                           \
         cudaError_t e = prep(k_tensor_hog<NN, JJ>, smem);                                \
         if (e != cudaSuccess) return e;                                                  \
-        k_tensor_hog<NN, JJ><<<grid, kTile, smem, s>>>(P, G, t_begin, t_end, eta,        \
-                                                       row_mean, core_part, H);          \
+        k_tensor_hog<NN, JJ><<<grid, kTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, \
+                                                       row_mean, core_step_scale, H);    \
         return cudaGetLastError();                                                       \
     }
     S3_FOR_EACH_TENSOR_SHAPE(X)

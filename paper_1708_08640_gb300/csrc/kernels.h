@@ -23,14 +23,39 @@ size_t tensor_hog_smem(int N, int JP, const int64_t* max_segs_per_factor, int n_
 cudaError_t launch_tensor_contrib(int N, int JP, const DParams& P, const DGroup& G,
                                   const TensorLaunch& L, cudaStream_t s);
 
-// HOGWILD: tiles [t_begin, t_end) on `grid` persistent CTAs; rows updated atomically with
-// step -eta * (sum or mean per tile); CTA core partials to core_part[blockIdx].
+// HOGWILD epoch: n_tiles tiles claimed from *tile_counter (zeroed by the caller) by `grid`
+// persistent CTAs; rows updated atomically with step -eta * damp * (sum or mean per tile);
+// each tile adds core_step_scale * eta * (its mean core step) to G atomically.
 // max_segs[F]: the largest number of segments of factor F in any tile (sizes the row
 // accumulators in shared memory; see tensor_hog_smem).
-cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G,
-                              int64_t t_begin, int64_t t_end, int grid, const float* eta,
-                              int row_mean, float* core_part, const int64_t* max_segs,
-                              cudaStream_t s);
+cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
+                              int* tile_counter, int grid, const float* eta, int row_mean,
+                              float core_step_scale, const int64_t* max_segs, cudaStream_t s);
+
+// BF16 tensor-core HOGWILD epoch (N = 3, JP = 16): as launch_tensor_hog, one CTA per SM;
+// sets *err_flag when a bounded wait on the tensor cores ran out.
+size_t tensor_hog_bf16_smem(int JP, const int64_t* max_segs, int nF);
+cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
+                                   int* tile_counter, int grid, const float* eta, int row_mean,
+                                   float core_step_scale, const int64_t* max_segs, int* err_flag,
+                                   cudaStream_t s);
+
+// Deterministic minibatch epoch as one cooperative launch of `grid` CTAs (see k_minibatch.cu).
+struct MbLaunch {
+    float* contrib[kMaxF];
+    float* core_part;        // >= grid partials of JP^N floats
+    unsigned* bar_count;     // zero before the launch
+    unsigned* bar_gen;
+    int* err_flag;
+    const float* eta;
+    float core_scale;
+    int row_mean;
+    int64_t n_batches;
+    int grid;
+};
+int minibatch_epoch_grid(int N, int JP, int num_sms);   // co-resident CTAs, 0 if none
+cudaError_t launch_minibatch_epoch(int N, int JP, const DParams& P, const DGroup& G,
+                                   const MbLaunch& L, cudaStream_t s);
 
 // Forward: x~ of n entries given as SoA index arrays; optional predictions out, optional
 // per-CTA compensated partial sums of (x - x~)^2 (2 floats per CTA).

@@ -273,4 +273,54 @@ struct CoreAcc {
     }
 };
 
+// One tile's core step added lock-free to the core in global memory: thread (q, slice) sums
+// its slice of the tile's entries for multi-index q and all JP values of the last mode, then
+// adds  sc * sum - rg * G  (rg only once, by slice 0) with atomics.
+template <int N, int JP>
+struct CoreTile {
+    static constexpr int JPR = round4(JP);
+    static constexpr int Q = ipow_t<JP, N - 1>::v;
+    static constexpr int KS = (kTile / Q) > 0 ? (kTile / Q) : 1;
+    static constexpr int QPT = (Q + kTile - 1) / kTile;
+
+    __device__ __forceinline__ static void apply(const float* __restrict__ stage, int nb,
+                                                 const float* __restrict__ sG, float* G,
+                                                 float sc, float rg) {
+        const int t = threadIdx.x;
+        const int slice = KS > 1 ? t / Q : 0;
+#pragma unroll
+        for (int k = 0; k < QPT; ++k) {
+            const int q = KS > 1 ? (t % Q) : (t + k * kTile);
+            if (slice >= KS || q >= Q) continue;
+            int jj[N - 1];
+            {
+                int r = q;
+#pragma unroll
+                for (int n = N - 2; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
+            }
+            float tile[JP];
+#pragma unroll
+            for (int j = 0; j < JP; ++j) tile[j] = 0.f;
+            for (int b = slice; b < nb; b += KS) {
+                float w = stage[(0 * kTile + b) * JPR + jj[0]];
+#pragma unroll
+                for (int n = 1; n < N - 1; ++n) w *= stage[(n * kTile + b) * JPR + jj[n]];
+                float r[JP];
+                load_grow<JP>(stage + ((N - 1) * kTile + b) * JPR, r);
+#pragma unroll
+                for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
+            }
+            float g[JP];
+            load_grow<JP>(sG + q * JPR, g);
+            float d[JPR];
+#pragma unroll
+            for (int j = 0; j < JPR; ++j)
+                d[j] = j < JP ? fmaf(sc, tile[j], slice == 0 ? -rg * g[j] : 0.f) : 0.f;
+#pragma unroll
+            for (int c = 0; c < JPR / 4; ++c)
+                red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+        }
+    }
+};
+
 }  // namespace s3

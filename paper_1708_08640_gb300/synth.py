@@ -83,6 +83,18 @@ def zipf_sample(rng, n, support, s):
     return perm[rank].astype(np.int64)
 
 
+def _merge_unique(keys, new):
+    """Sorted distinct values of keys (sorted, distinct) together with new: the same result
+    as numpy.unique(numpy.concatenate([keys, new])), by a stable sort and a neighbour test."""
+    s = np.sort(np.concatenate([keys, new]), kind="stable")
+    if s.shape[0] == 0:
+        return s
+    keep = np.empty(s.shape[0], dtype=bool)
+    keep[0] = True
+    np.not_equal(s[1:], s[:-1], out=keep[1:])
+    return s[keep]
+
+
 def _draw_coords(rng, n, dims, laws, perms):
     cols = []
     for d, law, perm in zip(dims, laws, perms):
@@ -117,7 +129,7 @@ def unique_coords(rng, n, dims, laws):
         draw = int(need * 1.15) + 64
         cols = _draw_coords(rng, draw, dims, laws, perms)
         k = np.ravel_multi_index(tuple(cols), dims).astype(np.int64)
-        keys = np.unique(np.concatenate([keys, k]))
+        keys = _merge_unique(keys, k)
         need = n - keys.shape[0]
     if keys.shape[0] > n:
         keys = rng.choice(keys, size=n, replace=False)
@@ -161,7 +173,7 @@ def _binary_symmetric(rng, n_entries, I, law):
         a, b = _draw_coords(rng, draw, (I, I), (law, law), (perm, perm))
         keep = a != b
         lo, hi = np.minimum(a, b)[keep], np.maximum(a, b)[keep]
-        keys = np.unique(np.concatenate([keys, lo * I + hi]))
+        keys = _merge_unique(keys, lo * I + hi)
         need = n_edges - keys.shape[0]
     if keys.shape[0] > n_edges:
         keys = rng.choice(keys, size=n_edges, replace=False)
@@ -287,6 +299,7 @@ PRESETS = {
     "cfg2_j32": lambda rng: _cfg1(rng, (32, 32, 32)),
     "cfg2_small_j16": lambda rng: _cfg1_small(rng, (16, 16, 16)),
     "cfg2_small_j32": lambda rng: _cfg1_small(rng, (32, 32, 32)),
+    "cfg2_tiny_j16": lambda rng: _cfg1_tiny(rng, (16, 16, 16)),
     "cfg3": _cfg3,
     "cfg3_small": _cfg3_small,
     "cfg3_tiny": _cfg3_tiny,

@@ -44,7 +44,7 @@ def _init(lib, idx, val, dims, J, coupled=(), order=None, hp=None):
         c = np.ascontiguousarray(c, dtype=np.int32)
         keep += [r, c]
         ys[m] = L.s3_coo_matrix(mode, rows, K, r.shape[0], r.ctypes.data, c.ctypes.data, None)
-    h = hp or L.s3_hparams(0.01, 0.1, 0.01, 1.0, 64, 1.0, 0, 0, 0, 0.0)
+    h = hp or L.s3_hparams(0.01, 0.1, 0.01, 1.0, 64, 1.0, 0, 0, 0.0, 0)
     Ja = (C.c_int * N)(*J)
     ordr = None if order is None else np.ascontiguousarray(order, dtype=np.int64)
     ctx = C.c_void_p()
@@ -112,9 +112,9 @@ def test_rejects_order_that_is_not_a_permutation(lib):
 
 def test_rejects_bad_hparams(lib):
     idx, val = _valid()
-    h = L.s3_hparams(-1.0, 0.1, 0.01, 1.0, 64, 1.0, 0, 0, 0, 0.0)
+    h = L.s3_hparams(-1.0, 0.1, 0.01, 1.0, 64, 1.0, 0, 0, 0.0, 0)
     assert _init(lib, idx, val, (5, 4, 3), (2, 2, 2), hp=h)[0] == L.S3_ERR_ARG
-    h = L.s3_hparams(0.01, 0.1, 0.01, 1.0, 0, 1.0, 0, 0, 0, 0.0)
+    h = L.s3_hparams(0.01, 0.1, 0.01, 1.0, 0, 1.0, 0, 0, 0.0, 0)
     assert _init(lib, idx, val, (5, 4, 3), (2, 2, 2), hp=h)[0] == L.S3_ERR_ARG
 
 
