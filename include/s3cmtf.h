@@ -196,6 +196,25 @@ enum { S3_K_ALL = -1, S3_K_TENSOR_HOG = 0, S3_K_TENSOR_MB = 1, S3_K_TENSOR_GRAD 
 int s3_profile(s3_ctx* ctx, int enable);
 int s3_profile_read(s3_ctx* ctx, int family, double* ms, int64_t* launches, int64_t* entries);
 
+/* Test RMSE without allocating: the same value as s3_rmse(ctx, test, 1, ...) for callers
+ * that cannot allocate device memory -- code running inside a CUDA graph capture, under a
+ * fixed memory budget, or next to an allocator that owns the whole device -- while s3_rmse
+ * may grow its reduction buffer with cudaMalloc.  The paper has no counterpart; it is a
+ * deployment variant of the reduction of Section 4.1's test RMSE.
+ *   idx       host array of N device pointers, each [n] (0-based int32 coordinates)
+ *   val       device [n] observed values
+ *   n         at most 2,097,152; larger n returns S3_ERR_ARG (split the call)
+ *   rmse_out  host; sqrt(sum (val - x~)^2 / n)
+ * Its only scratch is a 64 KiB static device array compiled into the library (every GPU
+ * that loads the library holds it until exit).  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the context's device current; make
+ * that first call before any stream capture.  Calls share the array: calls whose work
+ * overlaps on the GPU (other host threads, other streams) race on it and must be
+ * serialised by the caller.  Enqueues on the context's stream and synchronises it.
+ * Indices are not validated (they are device memory). */
+int s3_rmse_noalloc(s3_ctx* ctx, const int32_t* const* idx, const float* val, int64_t n,
+                    double* rmse_out);
+
 const char* s3_last_error(const s3_ctx* ctx);
 void s3_destroy(s3_ctx* ctx);
 

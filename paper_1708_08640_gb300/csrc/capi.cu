@@ -918,3 +918,16 @@ extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* co
     }
     return S3_OK;
 }
+
+// ------------------------------------------------------------------ accessors for noalloc.cu
+namespace s3 {
+const DParams* ctx_params(const s3_ctx* ctx, int* N, int* JP, cudaStream_t* stream, int* device) {
+    if (!usable(ctx)) return nullptr;
+    *N = ctx->N;
+    *JP = ctx->JP;
+    *stream = ctx->stream;
+    *device = ctx->device;
+    return &ctx->P;
+}
+int ctx_fail(s3_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }
+}  // namespace s3

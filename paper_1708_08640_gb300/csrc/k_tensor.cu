@@ -334,6 +334,26 @@ int tensor_hog_blocks_per_sm(int N, int JP, size_t smem) {
     return 0;
 }
 
+// the forward pass with one CTA per 256 entries (no grid-stride loop): ceil(n / 256) pairs
+cudaError_t launch_tensor_fwd_one_pass(int N, int JP, const DParams& P, const int32_t* const* idx,
+                                       const float* x, int64_t n, float* sq_part, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    IdxPtrs ip;
+    for (int m = 0; m < kMaxN; ++m) ip.p[m] = m < N ? idx[m] : nullptr;
+    const unsigned grid = (unsigned)((n + kTile - 1) / kTile);
+    const size_t smem = sizeof(float) * core_floats(N, JP);
+#define X(NN, JJ)                                                                      \
+    if (N == NN && JP == JJ) {                                                         \
+        cudaError_t e = prep(k_tensor_fwd<NN, JJ>, smem);                              \
+        if (e != cudaSuccess) return e;                                                \
+        k_tensor_fwd<NN, JJ><<<grid, kTile, smem, s>>>(P, ip, x, n, nullptr, sq_part); \
+        return cudaGetLastError();                                                     \
+    }
+    S3_FOR_EACH_TENSOR_SHAPE(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
 int tensor_fwd_blocks(int64_t n) {
     return (int)std::min<int64_t>((n + kTile - 1) / kTile, 4096);
 }
