@@ -89,6 +89,8 @@ def _lib_handle():
             lib.s3o_epoch_sequential.restype = C.c_int
             lib.s3o_epoch_minibatch.argtypes = [D, P, H, C.c_int64, lp, C.c_int64]
             lib.s3o_epoch_minibatch.restype = C.c_int
+            lib.s3o_finalize_qr.argtypes = [D, P, C.POINTER(dp)]
+            lib.s3o_finalize_qr.restype = C.c_int
             _lib = lib
     return _lib
 
@@ -272,3 +274,13 @@ class Oracle:
                                           order.shape[0])
         if rc != 0:
             raise ValueError("order holds an item outside the union of entries")
+
+    def finalize_qr(self):
+        """Algorithm 1's final step: U^(n) <- Q^(n), G <- G x_n R^(n), V_m <- V_m R^(c)^T
+        (thin QR with diag(R) > 0).  Returns the R^(n); raises if a factor is rank deficient."""
+        Rs = [np.zeros((j, j)) for j in self.J]
+        rc = self.lib.s3o_finalize_qr(C.byref(self.data), C.byref(self.params_c),
+                                      _ptr_array(Rs, C.c_double))
+        if rc != 0:
+            raise ValueError("a factor matrix does not have full column rank")
+        return Rs

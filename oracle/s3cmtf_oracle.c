@@ -14,6 +14,7 @@
  *   Eq. (8)  per-entry gradients                             (Section 3.2)
  *   Alg. 1   S3CMTF-naive epoch (lock-free SGD; here P = 1)  (Section 3.4)
  *   Alg. 2   compute_gradient                                (Section 3.4)
+ *   Alg. 1   final QR step (U <- Q, G <- G x_n R, V <- V R^T) (Section 3.4)
  *   Def. 4 / Def. 5 / Lemma 2 / Lemma 3 / Alg. 3: intermediate data S, Collapse and the
  *            division route of S3CMTF-opt                    (Section 3.5)
  *   test RMSE                                                (Section 4.1, "Measure")
@@ -633,5 +634,134 @@ int s3o_epoch_minibatch(const s3o_data* d, s3o_params* p, const s3o_hparams* hp,
     free(DV); free(hV); free(DG); free(eG); free(gu); free(gv); free(tf); free(tr);
     free_counts(cnt, N);
     free_counts(cntY, M);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ final QR step
+ * Algorithm 1, after the last epoch: for every mode n the thin QR decomposition
+ * U^(n) = Q^(n) R^(n) (Q^(n) I_n x J_n with orthonormal columns, R^(n) J_n x J_n upper
+ * triangular), U^(n) <- Q^(n), G <- G x_n R^(n); then every coupled factor
+ * V_m <- V_m R^(c_m)^T.  The factorisation is unchanged: x~ = (G x_1 R^(1) ... x_N R^(N))
+ * x_1 Q^(1) ... x_N Q^(N) and U^(c) V^T = Q^(c) (V R^(c)^T)^T (Section 3.4, description
+ * of Algorithm 1).  The paper does not fix the signs; here diag(R^(n)) > 0, which makes
+ * the thin QR of a full-column-rank matrix unique.
+ *
+ * Householder reflections in double precision.  R_out (optional): [N][J_n * J_n]
+ * row-major.  Returns 0, or -1 when some U^(n) does not have full column rank (a diagonal
+ * entry of R at most 1e-12 of the largest), in which case nothing is changed. */
+
+/* thin QR of A (rows x cols, row-major, rows >= cols) into Q (rows x cols) and R (cols x
+ * cols); diag(R) >= 0.  Returns -1 if A is numerically rank deficient. */
+static int householder_qr(const double* A, int64_t rows, int cols, double* Q, double* R) {
+    double* W = (double*)malloc(sizeof(double) * rows * cols);     /* working copy */
+    double* vs = (double*)calloc((size_t)rows * cols, sizeof(double)); /* reflectors */
+    memcpy(W, A, sizeof(double) * rows * cols);
+    int rc = 0;
+    for (int k = 0; k < cols; ++k) {
+        /* reflector v = x + sign(x_0) |x| e_0 on column k, rows k.. */
+        double nrm = 0.0;
+        for (int64_t i = k; i < rows; ++i) nrm += W[i * cols + k] * W[i * cols + k];
+        nrm = sqrt(nrm);
+        double* v = vs + (int64_t)k * rows;
+        if (nrm == 0.0) { rc = -1; continue; }
+        const double x0 = W[(int64_t)k * cols + k];
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        for (int64_t i = k; i < rows; ++i) v[i] = W[i * cols + k];
+        v[k] -= alpha;
+        double vn = 0.0;
+        for (int64_t i = k; i < rows; ++i) vn += v[i] * v[i];
+        vn = sqrt(vn);
+        if (vn == 0.0) continue;   /* column already of the form alpha e_k */
+        for (int64_t i = k; i < rows; ++i) v[i] /= vn;
+        /* W[k:, k:] -= 2 v (v^T W[k:, k:]) */
+        for (int c = k; c < cols; ++c) {
+            double s = 0.0;
+            for (int64_t i = k; i < rows; ++i) s += v[i] * W[i * cols + c];
+            for (int64_t i = k; i < rows; ++i) W[i * cols + c] -= 2.0 * v[i] * s;
+        }
+    }
+    /* R: upper triangle of W; Q = H_0 H_1 ... H_{cols-1} [I; 0] */
+    for (int r = 0; r < cols; ++r)
+        for (int c = 0; c < cols; ++c) R[r * cols + c] = c >= r ? W[(int64_t)r * cols + c] : 0.0;
+    memset(Q, 0, sizeof(double) * rows * cols);
+    for (int c = 0; c < cols; ++c) Q[(int64_t)c * cols + c] = 1.0;
+    for (int k = cols - 1; k >= 0; --k) {
+        const double* v = vs + (int64_t)k * rows;
+        for (int c = 0; c < cols; ++c) {
+            double s = 0.0;
+            for (int64_t i = k; i < rows; ++i) s += v[i] * Q[i * cols + c];
+            for (int64_t i = k; i < rows; ++i) Q[i * cols + c] -= 2.0 * v[i] * s;
+        }
+    }
+    /* numerical rank: every |R_rr| above 1e-12 of the largest */
+    double dmax = 0.0;
+    for (int r = 0; r < cols; ++r) dmax = fmax(dmax, fabs(R[r * cols + r]));
+    /* signs: diag(R) >= 0 (row r of R and column r of Q flip together) */
+    for (int r = 0; r < cols; ++r) {
+        if (!(fabs(R[r * cols + r]) > 1e-12 * dmax)) rc = -1;
+        if (R[r * cols + r] < 0.0) {
+            for (int c = 0; c < cols; ++c) R[r * cols + c] = -R[r * cols + c];
+            for (int64_t i = 0; i < rows; ++i) Q[i * cols + r] = -Q[i * cols + r];
+        }
+    }
+    free(W);
+    free(vs);
+    return rc;
+}
+
+/* G <- G x_n R: new G[.., i, ..] = sum_j R[i][j] G[.., j, ..] (mode n, last mode fastest) */
+static void core_times_matrix(int N, const int* J, double* G, int n, const double* R) {
+    const int64_t P = core_size(N, J);
+    int64_t inner = 1;
+    for (int k = n + 1; k < N; ++k) inner *= J[k];
+    const int64_t outer = P / (inner * J[n]);
+    double* col = (double*)malloc(sizeof(double) * J[n]);
+    for (int64_t o = 0; o < outer; ++o)
+        for (int64_t s = 0; s < inner; ++s) {
+            double* base = G + o * (int64_t)J[n] * inner + s;
+            for (int i = 0; i < J[n]; ++i) {
+                double acc = 0.0;
+                for (int j = 0; j < J[n]; ++j) acc += R[i * J[n] + j] * base[(int64_t)j * inner];
+                col[i] = acc;
+            }
+            for (int i = 0; i < J[n]; ++i) base[(int64_t)i * inner] = col[i];
+        }
+    free(col);
+}
+
+int s3o_finalize_qr(const s3o_data* d, s3o_params* p, double* const* R_out) {
+    const int N = d->N, M = d->M;
+    double** Q = (double**)malloc(sizeof(double*) * N);
+    double** R = (double**)malloc(sizeof(double*) * N);
+    int rc = 0;
+    for (int n = 0; n < N; ++n) {
+        Q[n] = (double*)malloc(sizeof(double) * d->I[n] * d->J[n]);
+        R[n] = (double*)malloc(sizeof(double) * d->J[n] * d->J[n]);
+        if (d->I[n] < d->J[n] || householder_qr(p->U[n], d->I[n], d->J[n], Q[n], R[n]) != 0) rc = -1;
+    }
+    if (rc == 0) {
+        for (int n = 0; n < N; ++n) {
+            memcpy(p->U[n], Q[n], sizeof(double) * d->I[n] * d->J[n]);
+            core_times_matrix(N, d->J, p->G, n, R[n]);
+            if (R_out && R_out[n]) memcpy(R_out[n], R[n], sizeof(double) * d->J[n] * d->J[n]);
+        }
+        for (int m = 0; m < M; ++m) {
+            const int c = d->cmode[m], Jc = d->J[c];
+            double* row = (double*)malloc(sizeof(double) * Jc);
+            for (int64_t k = 0; k < d->K[m]; ++k) {
+                double* v = p->V[m] + k * Jc;
+                for (int i = 0; i < Jc; ++i) {   /* (V R^T)[k][i] = sum_j V[k][j] R[i][j] */
+                    double acc = 0.0;
+                    for (int j = 0; j < Jc; ++j) acc += v[j] * R[c][i * Jc + j];
+                    row[i] = acc;
+                }
+                memcpy(v, row, sizeof(double) * Jc);
+            }
+            free(row);
+        }
+    }
+    for (int n = 0; n < N; ++n) { free(Q[n]); free(R[n]); }
+    free(Q);
+    free(R);
     return rc;
 }

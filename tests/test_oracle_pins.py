@@ -309,3 +309,68 @@ def test_noiseless_planted_model_train_error_goes_to_zero():
         hist.append(o.rmse(p.train_idx, p.train_val))
     assert np.all(np.diff(hist[15:]) < 0)
     assert hist[-1] < 0.01
+
+
+# ------------------------------------------------------------------ Alg. 1: final QR step
+@pytest.mark.parametrize("dims,J,ncpl", [((30, 20, 10), (4, 3, 2), 2), ((9, 8, 7, 6), (3, 2, 3, 2), 2)])
+def test_finalize_qr_keeps_every_prediction(dims, J, ncpl):
+    """Section 3.4: replacing U by Q, G by G x_n R and V by V R^T is the same factorisation:
+    every tensor cell of the dense reconstruction and every coupled entry is unchanged."""
+    prob, params = random_problem(dims, J, nnz=60, n_coupled=ncpl, seed=7)
+    o = make(prob, params)
+    X0 = dense_tucker(params[0], params[1])
+    cpl0 = [o.predict_coupled(m, c.rows, c.cols) for m, c in enumerate(prob.coupled)]
+    o.finalize_qr()
+    G1, U1, _ = o.get_params()
+    np.testing.assert_allclose(dense_tucker(G1, U1), X0, rtol=1e-11, atol=1e-12)
+    for m, c in enumerate(prob.coupled):
+        np.testing.assert_allclose(o.predict_coupled(m, c.rows, c.cols), cpl0[m], rtol=1e-11,
+                                   atol=1e-12)
+
+
+def test_finalize_qr_is_the_thin_qr_with_positive_diagonal():
+    """U_old = Q R with Q^T Q = I and R upper triangular, diag(R) > 0: the same Q and R as
+    numpy's (LAPACK) QR after its signs are made positive."""
+    prob, params = random_problem((40, 25, 12), (5, 4, 3), nnz=50, n_coupled=1, seed=8)
+    o = make(prob, params)
+    Rs = o.finalize_qr()
+    _, U1, _ = o.get_params()
+    for n, (u0, q, r) in enumerate(zip(params[1], U1, Rs)):
+        np.testing.assert_allclose(q.T @ q, np.eye(q.shape[1]), atol=1e-13)
+        np.testing.assert_allclose(q @ r, u0, rtol=1e-12, atol=1e-13)
+        assert np.all(np.tril(r, -1) == 0.0) and np.all(np.diag(r) > 0)
+        ql, rl = np.linalg.qr(u0)
+        s = np.sign(np.diag(rl))
+        np.testing.assert_allclose(q, ql * s, atol=1e-12)
+        np.testing.assert_allclose(r, s[:, None] * rl, atol=1e-12)
+
+
+def test_finalize_qr_rank_one_by_hand():
+    """J = 1: Q = u / |u|, R = |u|, so G becomes G |u1| |u2| |u3| and V becomes V |u_c|."""
+    prob, params = random_problem((6, 5, 4), (1, 1, 1), nnz=10, n_coupled=1, seed=9)
+    o = make(prob, params)
+    G, U, V = params
+    norms = [np.linalg.norm(u[:, 0]) for u in U]
+    o.finalize_qr()
+    G1, U1, V1 = o.get_params()
+    np.testing.assert_allclose(G1.ravel(), G.ravel() * np.prod(norms), rtol=1e-13)
+    for u, u1, nm in zip(U, U1, norms):
+        np.testing.assert_allclose(u1[:, 0], u[:, 0] / nm, rtol=1e-13)
+    np.testing.assert_allclose(V1[0], V[0] * norms[prob.coupled[0].mode], rtol=1e-13)
+
+
+def test_finalize_qr_is_idempotent_and_rejects_rank_deficiency():
+    prob, params = random_problem((20, 15, 10), (3, 3, 2), nnz=30, n_coupled=1, seed=10)
+    o = make(prob, params)
+    o.finalize_qr()
+    p1 = o.get_params()
+    for r in o.finalize_qr():                 # orthonormal factors: R = I
+        np.testing.assert_allclose(r, np.eye(r.shape[0]), atol=1e-13)
+    p2 = o.get_params()
+    np.testing.assert_allclose(p2[0], p1[0], atol=1e-13)
+    G, U, V = params
+    U = [u.copy() for u in U]
+    U[1][:, 2] = U[1][:, 0]                   # dependent columns
+    o2 = make(prob, (G, U, V))
+    with pytest.raises(ValueError):
+        o2.finalize_qr()
