@@ -647,8 +647,8 @@ int s3o_epoch_minibatch(const s3o_data* d, s3o_params* p, const s3o_hparams* hp,
  * the thin QR of a full-column-rank matrix unique.
  *
  * Householder reflections in double precision.  R_out (optional): [N][J_n * J_n]
- * row-major.  Returns 0, or -1 when some U^(n) does not have full column rank (a diagonal
- * entry of R at most 1e-12 of the largest), in which case nothing is changed. */
+ * row-major.  Returns 0, or -1 when some U^(n) does not have full numerical column rank (a
+ * diagonal entry of R at most 1e-7 of the largest), in which case nothing is changed. */
 
 /* thin QR of A (rows x cols, row-major, rows >= cols) into Q (rows x cols) and R (cols x
  * cols); diag(R) >= 0.  Returns -1 if A is numerically rank deficient. */
@@ -693,12 +693,13 @@ static int householder_qr(const double* A, int64_t rows, int cols, double* Q, do
             for (int64_t i = k; i < rows; ++i) Q[i * cols + c] -= 2.0 * v[i] * s;
         }
     }
-    /* numerical rank: every |R_rr| above 1e-12 of the largest */
+    /* numerical rank: every |R_rr| above 1e-7 of the largest (what a Gram-based QR in
+     * double precision can still resolve: its pivots are R_rr^2) */
     double dmax = 0.0;
     for (int r = 0; r < cols; ++r) dmax = fmax(dmax, fabs(R[r * cols + r]));
     /* signs: diag(R) >= 0 (row r of R and column r of Q flip together) */
     for (int r = 0; r < cols; ++r) {
-        if (!(fabs(R[r * cols + r]) > 1e-12 * dmax)) rc = -1;
+        if (!(fabs(R[r * cols + r]) > 1e-7 * dmax)) rc = -1;
         if (R[r * cols + r] < 0.0) {
             for (int c = 0; c < cols; ++c) R[r * cols + c] = -R[r * cols + c];
             for (int64_t i = 0; i < rows; ++i) Q[i * cols + r] = -Q[i * cols + r];
