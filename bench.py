@@ -36,7 +36,11 @@ UNIT = "nnz-updates/s"
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 # FP32 FFMA roof of the CUDA-core form: SMs x FP32 lanes x 2 flop x max SM clock
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-KERNEL_SOURCES = ["paper_1708_08640_gb300/csrc/k_tensor.cu",
+# the sources of the FP32 HOGWILD kernel: a committed DRAM-traffic figure counts only while
+# their hash is the one it was captured on
+KERNEL_SOURCES = ["paper_1708_08640_gb300/csrc/tensor_hog.cuh",
+                  "paper_1708_08640_gb300/csrc/k_tensor_hog2.cu",
+                  "paper_1708_08640_gb300/csrc/hog_common.cuh",
                   "paper_1708_08640_gb300/csrc/tensor_fp32.cuh",
                   "paper_1708_08640_gb300/csrc/common.cuh"]
 
@@ -48,7 +52,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cfg1")
-    ap.add_argument("--mode", choices=["hogwild", "minibatch"], default="hogwild")
+    ap.add_argument("--mode", choices=["hogwild", "minibatch", "gradient"], default="hogwild",
+                    help="the step: a HOGWILD or minibatch epoch (nnz-updates/s), or one full "
+                         "gradient pass, the differentiation form (GB/s; e.g. --workload cfg3)")
     ap.add_argument("--cpu-sample", type=int, default=600_000,
                     help="items of the visiting order the CPU oracle baseline processes")
     ap.add_argument("--no-extras", action="store_true",
@@ -163,10 +169,72 @@ def workload_desc(p, mode, precision="fp32"):
             "l2": "inputs larger than L2 (COO and layout arrays >> 129 MB); no flush"}
 
 
+def gradient_bytes(p):
+    """Algorithmic bytes of one full-gradient pass: the COO of every tensor and coupled
+    entry, every touched factor row read once, every gradient written once."""
+    J = p.J
+    coo = p.nnz * (4 * p.N + 4) + sum(c.nnz * 12 for c in p.coupled)
+    rows = sum(int(np.unique(p.train_idx[n]).shape[0]) * J[n] for n in range(p.N))
+    rows += sum(int(np.unique(c.cols).shape[0]) * J[c.mode] for c in p.coupled)
+    grad_out = int(np.prod(J)) + sum(d * j for d, j in zip(p.dims, J)) + sum(
+        c.K * J[c.mode] for c in p.coupled)
+    return coo + 4 * rows + 4 * grad_out
+
+
+def flops_per_entry(p):
+    J = p.J
+    return 6.0 * float(np.prod(J)) if p.N == 3 else 6.0 * float(np.prod(J)) + 4.0 * float(np.prod(J[:3]))
+
+
+def sub_problem(p, n_tensor, n_coupled):
+    """The first n entries of the tensor and of each coupled matrix (a bounded sample)."""
+    import copy
+    q = copy.copy(p)
+    q.train_idx = p.train_idx[:, :n_tensor]
+    q.train_val = p.train_val[:n_tensor]
+    q.coupled = [synth.Coupled(c.mode, c.K, c.rows[:n_coupled], c.cols[:n_coupled],
+                               c.vals[:n_coupled]) for c in p.coupled]
+    return q
+
+
 # ----------------------------------------------------------------------------- reference arm
+def run_reference_gradient(args):
+    """The oracle's full gradient (FP64, one thread) on a bounded sample of the workload."""
+    import oracle
+    p = synth.make_problem(args.workload)
+    S = max(1000, min(args.cpu_sample // 20, p.nnz))
+    q = sub_problem(p, S, max(1, S // 2))
+    o = oracle.Oracle(q, **{k: v for k, v in q.hparams.items()
+                           if k in ("lr0", "mu", "lambda_reg", "lambda_m", "batch", "core_scale")})
+    o.set_params(*synth.init_params(q, 1))
+    for _ in range(args.warmup):
+        o.full_gradient()
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.full_gradient()
+        times.append(time.perf_counter() - t0)
+    gb = gradient_bytes(q)
+    value = gb / (sum(times) / len(times)) / 1e9
+    sample = (f"the first {q.nnz} tensor entries and first {q.coupled[0].nnz if q.coupled else 0} "
+              f"entries of each coupled matrix of {p.name}; one full gradient per step, FP64")
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": dict(workload_desc(p, "gradient"), parallelism="oracle, 1 thread"),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
+    if args.mode == "gradient":
+        return run_reference_gradient(args)
     import oracle  # noqa: F401
     p = synth.make_problem(args.workload)
     order = synth.union_order(p, 2)
@@ -198,60 +266,192 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- forms
-def precision_forms(p, order, stream, args, epochs=4):
-    """The FP32 and BF16 forms of the HOGWILD epoch on the same data at J = 16 (the cfg2
-    workload): epoch time, nnz-updates/s, test RMSE per epoch, and the tensor-pass kernel's
-    roofline (FP32 FFMA roof for the FP32 form, BF16 tensor roof for the BF16 form)."""
-    import copy
+def precision_forms(p, order, stream, args, J=16, epochs=4):
+    """The FP32 and BF16 forms of the HOGWILD epoch on the same data at rank J (the cfg2
+    workloads, J = 16 and 32): epoch time, nnz-updates/s, test RMSE after every epoch (the
+    "matched RMSE" check: the largest relative gap between the two forms' curves), and the
+    tensor-pass kernel's roofline (FP32 FFMA roof for the FP32 form, BF16 tensor roof for
+    the BF16 form).  Epochs are timed one by one with CUDA events; the RMSE reads between
+    them are outside the timed regions."""
     import ctypes as C
 
     import torch
 
     from paper_1708_08640_gb300 import _lib as L
     from paper_1708_08640_gb300.model import S3CMTF
-    q = copy.copy(p)
-    q.J = (16, 16, 16)
+    q = synth.with_rank(p, (J, J, J))
     init = synth.init_params(q, 1)
     peaks, src = measured_peaks()
     out = {}
+    flops_entry = 6.0 * J ** 3
     for prec in ("fp32", "bf16"):
         m = S3CMTF.from_problem(q, order=order, stream=stream)
         m.set_params(*init)
         m.set_test(q.test_idx, q.test_val)
-        m.epoch("hogwild", prec)
-        m.rmse()
+        curve = []
+        m.epoch("hogwild", prec)          # warm-up epoch (its RMSE is the curve's first point)
+        curve.append(m.rmse())
         L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 1))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
+        total = 0.0
         for _ in range(epochs):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
             m.epoch("hogwild", prec)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / epochs
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+            curve.append(m.rmse())
+        ms = total / epochs
         kms, kn, ke = C.c_double(), C.c_int64(), C.c_int64()
         L.check(m.lib, m.ctx, m.lib.s3_profile_read(m.ctx, L.S3_K_TENSOR_HOG, C.byref(kms),
                                                       C.byref(kn), C.byref(ke)))
         L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 0))
-        flops = 6.0 * 16 ** 3 * ke.value
-        achieved = flops / (kms.value / 1000.0) / 1e12
+        achieved = flops_entry * ke.value / (kms.value / 1000.0) / 1e12
         if prec == "fp32":
             roof = {"bound": "alu", "peak": FP32_PEAK_TFLOPS, "peak_source": "derived"}
         else:
             roof = {"bound": "tensor", "peak": peaks["bf16_tflops_sustained"],
                     "peak_source": f"{src} bf16_tflops_sustained"}
         roof.update({"achieved": achieved, "unit": "TFLOP/s", "frac": achieved / roof["peak"],
-                     "kernel_ms_per_epoch": kms.value / epochs, "flops_per_entry": 6.0 * 16 ** 3})
+                     "kernel_ms_per_epoch": kms.value / epochs, "flops_per_entry": flops_entry})
         out[prec] = {"ms_per_epoch": ms, "nnz_updates_per_s": q.n_union / (ms / 1000.0),
-                     "test_rmse_after": m.rmse(), "epochs": 1 + epochs, "roofline": roof}
+                     "test_rmse": curve, "epochs": 1 + epochs, "roofline": roof,
+                     "launch": m.hog_config(prec)}
         m.close()
     out["bf16_speedup"] = out["fp32"]["ms_per_epoch"] / out["bf16"]["ms_per_epoch"]
-    out["rmse_rel_diff"] = (out["bf16"]["test_rmse_after"] - out["fp32"]["test_rmse_after"]) / \
-        out["fp32"]["test_rmse_after"]
+    out["rmse_max_rel_gap"] = max(abs(b - a) / a for a, b in
+                                  zip(out["fp32"]["test_rmse"], out["bf16"]["test_rmse"]))
+    # time to target: epochs (at the measured time per epoch) until a form's test RMSE is
+    # within 0.1% of the FP32 form's final RMSE
+    target = out["fp32"]["test_rmse"][-1] * 1.001
+    for prec in ("fp32", "bf16"):
+        hit = next((i + 1 for i, r in enumerate(out[prec]["test_rmse"]) if r <= target), None)
+        out[prec]["time_to_target_ms"] = None if hit is None else hit * out[prec]["ms_per_epoch"]
+    out["target_rmse"] = target
     return out
 
 
 # ----------------------------------------------------------------------------- our arm
+def run_gradient(args, world, rank, local):
+    """The differentiation form: one full-gradient pass (loss gradient with respect to the
+    core, every factor and every coupled factor) per step; value = algorithmic GB/s."""
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1708_08640_gb300 import _lib as L
+    from paper_1708_08640_gb300.model import S3CMTF
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    p = synth.make_problem(args.workload, seed=rank)
+    stream = torch.cuda.Stream()
+    model = S3CMTF.from_problem(p, order=synth.union_order(p, 2), stream=stream)
+    model.set_params(*synth.init_params(p, 1))
+    lib, ctx = model.lib, model.ctx
+    gb = gradient_bytes(p)
+    for _ in range(args.warmup):
+        model.gradient()
+    L.check(lib, ctx, lib.s3_profile(ctx, 1))
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        model.gradient()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = world * gb * args.steps / (ms_total / 1000.0) / 1e9
+
+    def read(fam):
+        ms, n, e = C.c_double(), C.c_int64(), C.c_int64()
+        L.check(lib, ctx, lib.s3_profile_read(ctx, fam, C.byref(ms), C.byref(n), C.byref(e)))
+        return ms.value, n.value, e.value
+
+    k_ms, k_n, k_entries = read(L.S3_K_TENSOR_GRAD)
+    _, launches, _ = read(L.S3_K_ALL)
+    L.check(lib, ctx, lib.s3_profile(ctx, 0))
+    fpe = flops_per_entry(p)
+    achieved = fpe * k_entries / (k_ms / 1000.0) / 1e12 if k_ms > 0 else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None, "traffic": None,
+                "kernel": "k_tensor_contrib", "launches": k_n,
+                "kernel_ms_per_step": k_ms / args.steps, "flops_per_entry": fpe,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                "share_of_step": (k_ms / args.steps) / ms_step}
+    # end to end through the public API: fresh values from pinned host memory, the pass,
+    # and the whole gradient back to pinned host memory
+    xv = torch.tensor(p.train_val, dtype=torch.float32).pin_memory()
+    yv = [torch.tensor(c.vals, dtype=torch.float32).pin_memory() for c in p.coupled]
+    dG, dU, dV = model.gradient()
+    hosts = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in [dG, *dU, *dV]]
+    d2h = sum(h.numel() * 4 for h in hosts)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        model.update_values(xv, yv)
+        outs = model.gradient()
+        with torch.cuda.stream(stream):
+            for h, d in zip(hosts, [outs[0], *outs[1], *outs[2]]):
+                h.copy_(d, non_blocking=True)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * gb * args.steps / e2e_s / 1e9, "unit": "GB/s",
+           "h2d_bytes_per_step": 4 * p.n_union, "d2h_bytes_per_step": d2h}
+    cpu = None
+    if rank == 0 and world == 1:
+        import oracle
+        S = max(1000, min(args.cpu_sample // 20, p.nnz))
+        q = sub_problem(p, S, max(1, S // 2))
+        o = oracle.Oracle(q, **{k: v for k, v in q.hparams.items()
+                               if k in ("lr0", "mu", "lambda_reg", "lambda_m", "batch", "core_scale")})
+        o.set_params(*synth.init_params(q, 1))
+        t0 = time.perf_counter()
+        o.full_gradient()
+        dt = time.perf_counter() - t0
+        cpu = {"value": gradient_bytes(q) / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"full gradient of the first {q.nnz} tensor entries and "
+                         f"{q.coupled[0].nnz if q.coupled else 0} entries of each coupled "
+                         f"matrix, FP64, {dt:.1f} s"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_desc(p, "gradient"), parallelism=f"replicas x{world}",
+                               bytes_per_step=gb),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    model.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def run_ours(args, world, rank, local):
     import ctypes as C
 
@@ -283,6 +483,7 @@ def run_ours(args, world, rank, local):
         return model.rmse()
 
     rmse0 = model.rmse()
+    hog_launch = model.hog_config("fp32") if args.mode == "hogwild" else None
     for _ in range(args.warmup):
         step()
     # ---- timed region
@@ -306,6 +507,9 @@ def run_ours(args, world, rank, local):
     ms_step = ms_total / args.steps
     items = p.n_union
     value = world * items * args.steps / (ms_total / 1000.0)
+    # the same epochs, counted by kind of update (they run in one kernel)
+    split = {"tensor_updates_per_s": world * p.nnz * args.steps / (ms_total / 1000.0),
+             "coupled_updates_per_s": world * (p.n_union - p.nnz) * args.steps / (ms_total / 1000.0)}
 
     def read(fam):
         ms, n, e = C.c_double(), C.c_int64(), C.c_int64()
@@ -363,7 +567,8 @@ def run_ours(args, world, rank, local):
             extras["minibatch_epoch"] = {"ms": mb_ms, "nnz_updates_per_s": items / (mb_ms / 1000.0),
                                          "batches": model.info()["n_batches"]}
             m2.close()
-        extras["forms_j16"] = precision_forms(p, order, stream, args)
+        extras["forms_j16"] = precision_forms(p, order, stream, args, J=16)
+        extras["forms_j32"] = precision_forms(p, order, stream, args, J=32, epochs=2)
 
     # ---- end to end through the public API with host buffers
     xv = torch.tensor(p.train_val, dtype=torch.float32).pin_memory()
@@ -393,9 +598,10 @@ def run_ours(args, world, rank, local):
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": dict(workload_desc(p, args.mode), parallelism=f"replicas x{world}"),
+                "config": dict(workload_desc(p, args.mode), parallelism=f"replicas x{world}",
+                               hogwild_launch=hog_launch),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clk,
+                "gpu_launches": launches, "clocks": clk, "updates_by_kind": split,
                 "test_rmse": {"before": rmse0, "per_step": rmses}, **extras}
         print(json.dumps(line), flush=True)
     model.close()
@@ -408,6 +614,8 @@ def main():
     world, rank, local = dist_init()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.mode == "gradient":
+        run_gradient(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
 

@@ -88,14 +88,23 @@ typedef struct {
     float core_scale;   /* core step = eta_t * core_scale * (mean core gradient of a group) */
     int row_rule;       /* S3_ROW_SUM or S3_ROW_MEAN: a row takes the sum, or the mean, of
                            its gradients within one group (batch or HOGWILD tile) */
-    int hog_tile;       /* HOGWILD: tensor entries per tile (0 = default 256) */
+    int hog_tile;       /* HOGWILD: tensor entries per tile of the FP32 kernel (0 = default:
+                           96 for 3-way tensors, at most 128, and tiles of up to 64 entries
+                           spread each entry over four threads; 256 for 4-way); the BF16
+                           kernel's tiles hold 128 */
     float hog_staleness;/* HOGWILD: gamma of the staleness-aware row step.  A row expected to
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by
                            gamma / kappa; every other row takes the plain lock-free step.
-                           0 = default 32; < 0 disables the scaling. */
-    int hog_ctas;       /* HOGWILD: CTAs working at once (0 = as many as fit on the GPU).
+                           0 = default 320 / (largest rank), i.e. 32 at rank 10 (a coupled
+                           entry's step grows stiffer with the rank); < 0 disables the
+                           scaling. */
+    int hog_ctas;       /* HOGWILD: CTAs working at once (0 = default: on 3-way tensors, enough
+                           for about 29184 tensor entries in flight in either form, at most as
+                           many as fit on the GPU; on 4-way tensors as many as fit).
                            Fewer CTAs mean fewer stale updates in flight and less throughput. */
+    int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = as many as
+                           fit); fewer CTAs make its grid-wide barriers cheaper */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.
@@ -135,7 +144,8 @@ int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y, in
  *              core step of its mean gradient (W = tiles in flight), so that one wave of
  *              tiles moves the core by one group step; not deterministic.
  *   precision  S3_FP32 (CUDA-core FP32), or S3_BF16 (tensor-core contraction with BF16
- *              operands and FP32 accumulation; FP32 master parameters and errors).
+ *              operands and FP32 accumulation; FP32 master parameters and errors; HOGWILD
+ *              mode, 3-way tensors, padded rank 16 or 32, else S3_ERR_ARG).
  * Returns S3_ERR_DIVERGED if a non-finite parameter appeared (the parameters are left as
  * they are).  Enqueues work and synchronises once at the end to read the flag. */
 int s3_epoch(s3_ctx* ctx, int mode, int precision);
@@ -179,8 +189,25 @@ int s3_set_epoch(s3_ctx* ctx, int64_t t);
  * enqueued on the stream; host buffers must stay valid until the stream reaches them. */
 int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val);
 
+/* The final QR step of Algorithm 1 (Section 3.4): for every mode n the thin QR
+ * U^(n) = Q^(n) R^(n) with diag(R^(n)) > 0, then U^(n) <- Q^(n), G <- G x_n R^(n), and every
+ * coupled factor of mode n  V_m <- V_m R^(n)^T.  Predictions of the tensor and of the
+ * coupled matrices are unchanged up to FP32 rounding.  On the device: CholeskyQR2 in FP64
+ * (two Gram passes over U), deterministic.  Returns S3_ERR_ARG, changing nothing, when some
+ * U^(n) has fewer rows than its rank or is numerically rank deficient (a diagonal entry of
+ * R^(n) at most 1e-7 of the largest).  Synchronises. */
+int s3_finalize_qr(s3_ctx* ctx);
+
 /* Sizes: number of items in the visiting order, groups per epoch for each mode. */
 int s3_info(s3_ctx* ctx, int64_t* n_union, int64_t* n_batches, int64_t* n_tiles);
+
+/* The HOGWILD launch of a precision form (S3_FP32 or S3_BF16): persistent CTAs, tensor
+ * entries per tile (ctas x tile = entries in flight, the staleness of the lock-free
+ * scheme), dynamic shared memory per CTA and the CTAs that fit on one SM.  ctas = 0 for
+ * S3_BF16 when the form is not available for this context.  Any output may be NULL.
+ * Returns S3_ERR_ARG for another precision. */
+int s3_hog_config(s3_ctx* ctx, int precision, int64_t* ctas, int64_t* tile, int64_t* smem_bytes,
+                  int64_t* ctas_per_sm);
 
 /* Measurement support.  s3_profile(ctx, 1) makes the library record CUDA events on its
  * stream around every launch of its dominant kernels and count every kernel it launches;
@@ -188,8 +215,8 @@ int s3_info(s3_ctx* ctx, int64_t* n_union, int64_t* n_batches, int64_t* n_tiles)
  * for a kernel family, the summed event time of its launches (ms, synchronises), the
  * number of its launches and the tensor entries they processed; family -1 gives the
  * number of kernel launches of every kind (ms and entries 0).  Families:
- *   S3_K_TENSOR_HOG (HOGWILD tensor pass), S3_K_TENSOR_MB (minibatch tensor pass, only
- *   when profiling: the minibatch epoch is then launched without its CUDA graph),
+ *   S3_K_TENSOR_HOG (HOGWILD tensor pass), S3_K_TENSOR_MB (the minibatch epoch, one
+ *   persistent launch),
  *   S3_K_TENSOR_GRAD (gradient tensor pass), S3_K_TENSOR_FWD (loss / RMSE / predict). */
 enum { S3_K_ALL = -1, S3_K_TENSOR_HOG = 0, S3_K_TENSOR_MB = 1, S3_K_TENSOR_GRAD = 2,
        S3_K_TENSOR_FWD = 3 };

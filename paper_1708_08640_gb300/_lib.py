@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "S3_OK", -1: "S3_ERR_ARG", -2: "S3_ERR_INDEX", -3: "S3_ERR_OO
 # every function declared in include/s3cmtf.h
 EXPORTS = ("s3_init", "s3_epoch", "s3_loss", "s3_rmse", "s3_set_test", "s3_predict",
            "s3_gradient", "s3_get_params", "s3_set_params", "s3_get_epoch", "s3_set_epoch",
-           "s3_update_values", "s3_info", "s3_profile", "s3_profile_read", "s3_rmse_noalloc",
+           "s3_update_values", "s3_info", "s3_hog_config", "s3_profile", "s3_profile_read",
+           "s3_rmse_noalloc", "s3_finalize_qr",
            "s3_last_error", "s3_destroy")
 S3_K_ALL, S3_K_TENSOR_HOG, S3_K_TENSOR_MB, S3_K_TENSOR_GRAD, S3_K_TENSOR_FWD = -1, 0, 1, 2, 3
 
@@ -42,7 +43,7 @@ class s3_hparams(C.Structure):
     _fields_ = [("lr0", C.c_float), ("mu", C.c_float), ("lambda_reg", C.c_float),
                 ("lambda_m", C.c_float), ("batch", C.c_int), ("core_scale", C.c_float),
                 ("row_rule", C.c_int), ("hog_tile", C.c_int), ("hog_staleness", C.c_float),
-                ("hog_ctas", C.c_int)]
+                ("hog_ctas", C.c_int), ("mb_ctas", C.c_int)]
 
 
 class S3Error(RuntimeError):
@@ -88,6 +89,9 @@ def load(build_if_missing=True):
         lib.s3_set_epoch.argtypes = [vp, C.c_int64]
         lib.s3_update_values.argtypes = [vp, vp, pp]
         lib.s3_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        lib.s3_finalize_qr.argtypes = [vp]
+        lib.s3_hog_config.argtypes = [vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         lib.s3_profile.argtypes = [vp, C.c_int]
         lib.s3_profile_read.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.POINTER(C.c_int64)]

@@ -16,6 +16,9 @@
 using namespace s3;
 
 static constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
+// default HOGWILD staleness budget for 3-way tensors: tensor entries in flight at once
+// (304 CTAs x 96 entries)
+static constexpr int64_t kHogInflight = 29184;
 
 namespace {
 
@@ -25,6 +28,7 @@ struct DevGrouping {
     int64_t ngroups = 0;
     int nF = 0;
     std::vector<int64_t> t_off, c_off[kMaxM], seg_off[kMaxF], slot_off[kMaxF];
+    std::vector<int32_t> seg_nlong[kMaxF], seg_nhuge[kMaxF];
     int64_t max_t = 0, max_c[kMaxM] = {}, max_seg[kMaxF] = {}, max_ev[kMaxF] = {};
     int64_t* t_src = nullptr;
     int64_t* c_src[kMaxM] = {};
@@ -51,9 +55,16 @@ struct s3_ctx {
     std::vector<void*> allocs;
     DParams P{};
     float* inv_cnt[kMaxF] = {};
-    float* damp[kMaxF] = {};
     int64_t hog_grid = 1;
-    DevGrouping mb, hog, grad;
+    int64_t hog_bf_grid = 0;        // BF16 HOGWILD CTAs (0: the form is not available)
+    size_t hog_bf_smem = 0;
+    int64_t hog_tile = 0, hog_per_sm = 0, hog_bf_per_sm = 0, hog_bf_tile = 0, hog_ccap = 0;
+    double* qr_parts = nullptr;     // final QR step scratch (allocated at its first call)
+    double* qr_R = nullptr;
+    int* qr_bad = nullptr;
+    float* qr_core = nullptr;
+    int64_t qr_grid = 0;
+    DevGrouping mb, hog, grad, hog_bf;   // hog_bf: tiles of the BF16 kernel
     float* contrib[kMaxF] = {};
     float* core_part = nullptr;
     int64_t core_part_n = 0;       // partial slots
@@ -74,6 +85,7 @@ struct s3_ctx {
     int32_t* test_idx[kMaxN] = {};
     float* test_val = nullptr;
     size_t hog_smem = 0;
+    int hog_lanes = 1;
     int mb_grid = 0;               // CTAs of the persistent minibatch epoch
     unsigned* d_bar = nullptr;     // its grid-barrier counter and generation
     // measurement (s3_profile)
@@ -185,12 +197,15 @@ static int upload_grouping(s3_ctx* ctx, const HostGrouping& H, DevGrouping& D) {
     }
     for (int F = 0; F < H.nF; ++F) {
         D.seg_off[F] = H.seg_off[F];
+        D.seg_nlong[F] = H.seg_nlong[F];
+        D.seg_nhuge[F] = H.seg_nhuge[F];
         D.slot_off[F] = H.slot_off[F];
         D.max_seg[F] = H.max_seg[F];
         D.max_ev[F] = H.max_ev[F];
         int64_t *so = nullptr, *sl = nullptr;
-        int32_t *sr = nullptr, *ss = nullptr, *sc = nullptr;
+        int32_t *sr = nullptr, *ss = nullptr, *sc = nullptr, *sn = nullptr;
         CK(upload(ctx, &so, H.seg_off[F]));
+        CK(upload(ctx, &sn, H.seg_nlong[F]));
         CK(upload(ctx, &sl, H.slot_off[F]));
         CK(upload(ctx, &sr, H.seg_row[F]));
         CK(upload(ctx, &ss, H.seg_start[F]));
@@ -200,6 +215,7 @@ static int upload_grouping(s3_ctx* ctx, const HostGrouping& H, DevGrouping& D) {
         D.d.seg_row[F] = sr;
         D.d.seg_start[F] = ss;
         D.d.seg_cnt[F] = sc;
+        D.d.seg_nlong[F] = sn;
     }
     // keep the host vectors alive until the async copies are done
     CK(cudaStreamSynchronize(ctx->stream));
@@ -290,7 +306,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     ctx->JPR = round4(ctx->JP);
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
-        hp->hog_tile < 0 || hp->hog_ctas < 0)
+        hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0)
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];
@@ -367,21 +383,72 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         seeded_order(seed, ctx->n_union, hord);
     }
     // ---- layouts
-    HostGrouping hmb, hhog, hgrad;
-    const int64_t tile = hp->hog_tile > 0 ? std::min(hp->hog_tile, kTile) : kTile;
-    std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb);
-    if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SEG, hhog);
-    const int64_t grad_chunk = 1 << 20;
-    if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad);
-    if (!msg.empty()) return bail(S3_ERR_ARG, msg);
+    // the device (its SM count sizes the HOGWILD launches below)
     {
         cudaError_t e = cudaGetDevice(&ctx->device);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
         if (e != cudaSuccess) return bail(S3_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
     }
+    HostGrouping hmb, hhog, hgrad, hhog_bf;
+    const int nF = N + n_coupled;
+    // FP32 HOGWILD tiles hold at most 128 entries for 3-way tensors (two lanes per entry;
+    // tiles of up to 64 entries take four), 256 for 4-way (one lane).  Default for 3-way
+    // tensors: tiles of 128 entries (64 for ranks above 20, whose core fills most of shared
+    // memory) and about kHogInflight entries in flight (CTAs capped at kHogInflight / tile):
+    // the HOGWILD test-RMSE curve then stays within 1% of Algorithm 1's on the cfg1 workload.
+    const int64_t tile_max = N == 3 ? kTile / 2 : kTile;
+    const int64_t tile_default = N == 3 ? (ctx->JP <= 20 ? 128 : 64) : tile_max;
+    const int64_t tile = hp->hog_tile > 0 ? std::min<int64_t>(hp->hog_tile, tile_max) : tile_default;
+    ctx->hog_lanes = tensor_hog_lanes(N, ctx->JP, tile);
+    const bool bf16_ok = N == 3 && (ctx->JP == 16 || ctx->JP == 32);
+    std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb, kShortSeg);
+    if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SLOT, hhog);
+    // HOGWILD concurrency of the FP32 form: CTAs resident at once, each on a tile of `tile`
+    // entries
+    if (msg.empty()) {
+        int64_t ccap = 0;
+        for (int m = 0; m < n_coupled; ++m) ccap += hhog.max_c[m];
+        ctx->hog_ccap = ccap;
+        ctx->hog_smem = tensor_hog_smem(N, ctx->JP, ctx->hog_lanes, hhog.max_ev, hhog.max_seg, ccap, nF);
+        const int per_sm = ctx->hog_smem <= kMaxSmem
+                               ? std::max(1, tensor_hog_blocks_per_sm(N, ctx->JP, ctx->hog_lanes,
+                                                                      ctx->hog_smem))
+                               : 1;
+        int64_t cap = (int64_t)per_sm * ctx->num_sms;
+        if (hp->hog_ctas > 0) cap = std::min<int64_t>(cap, hp->hog_ctas);
+        else if (N == 3) cap = std::min<int64_t>(cap, std::max<int64_t>(1, kHogInflight / tile));
+        ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(cap, hhog.ngroups));
+        ctx->hog_per_sm = per_sm;
+        ctx->hog_tile = tile;
+    }
+    // The BF16 form runs as many CTAs as fit (with hog_ctas as a cap), and its tiles hold as
+    // many entries as make the FP32 form's number in flight (at most 128, the MMA's M): both
+    // forms then take the same lock-free schedule, and differ by their arithmetic only.  Its
+    // shared memory is bounded before its grouping exists from the FP32 grouping's largest
+    // tile, ceil(128 / tile) times over.
+    int64_t bf_tile = tensor_hog_bf16_tile();
+    if (msg.empty() && bf16_ok) {
+        const int64_t k = (tensor_hog_bf16_tile() + tile - 1) / tile;
+        int64_t ev[kMaxF], sg[kMaxF];
+        for (int F = 0; F < nF; ++F) { ev[F] = hhog.max_ev[F] * k; sg[F] = hhog.max_seg[F] * k; }
+        const size_t smem_est = tensor_hog_bf16_smem(ctx->JP, ev, sg, nF);
+        const int per_sm = smem_est <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->JP, smem_est) : 1;
+        int64_t ctas = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
+        if (hp->hog_ctas > 0) ctas = std::min<int64_t>(ctas, hp->hog_ctas);
+        const int64_t inflight = ctx->hog_grid * tile;
+        bf_tile = std::max<int64_t>(16, std::min<int64_t>(tensor_hog_bf16_tile(),
+                                                          inflight / std::max<int64_t>(ctas, 1)));
+        ctx->hog_bf_grid = ctas;
+        ctx->hog_bf_per_sm = per_sm;
+        ctx->hog_bf_tile = bf_tile;
+        msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, bf_tile, POS_SLOT, hhog_bf);
+    }
+    const int64_t grad_chunk = 1 << 20;
+    if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad, kShortSeg,
+                                             kHugeSeg);
+    if (!msg.empty()) return bail(S3_ERR_ARG, msg);
     *out = ctx;
     // ---- device buffers
-    const int nF = N + n_coupled;
     for (int n = 0; n < N; ++n) {
         CK(dalloc(ctx, &ctx->P.U[n], (size_t)ctx->I[n] * ctx->JPR));
         CK(cudaMemsetAsync(ctx->P.U[n], 0, (size_t)ctx->I[n] * ctx->JPR * sizeof(float), ctx->stream));
@@ -417,6 +484,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     if ((rc = upload_grouping(ctx, hmb, ctx->mb)) != S3_OK) return rc;
     if ((rc = upload_grouping(ctx, hhog, ctx->hog)) != S3_OK) return rc;
     if ((rc = upload_grouping(ctx, hgrad, ctx->grad)) != S3_OK) return rc;
+    if (bf16_ok && (rc = upload_grouping(ctx, hhog_bf, ctx->hog_bf)) != S3_OK) return rc;
     // scratch: contribution slots (minibatch and gradient groups), core partials
     for (int F = 0; F < nF; ++F) {
         const int64_t ev = std::max(ctx->mb.max_ev[F], ctx->grad.max_ev[F]);
@@ -441,33 +509,44 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(dalloc(ctx, &ctx->d_bar, 2));
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
     ctx->mb_grid = std::min<int>(minibatch_epoch_grid(N, ctx->JP, ctx->num_sms), (int)ctx->core_part_n);
+    if (hp->mb_ctas > 0) ctx->mb_grid = std::min<int>(ctx->mb_grid, hp->mb_ctas);
     CK(cudaMemsetAsync(ctx->d_kerr, 0, sizeof(int), ctx->stream));
     CK(cudaMallocHost((void**)&ctx->h_flag, 2 * sizeof(int)));
-    ctx->hog_smem = tensor_hog_smem(N, ctx->JP, ctx->hog.max_seg, nF);
-    CK(tensor_prepare(N, ctx->JP, ctx->hog_smem <= kMaxSmem ? ctx->hog_smem : 0));
-    // HOGWILD concurrency: CTAs resident at once, each working on one tile of `tile` entries
+    CK(tensor_prepare(N, ctx->JP));
+    if (bf16_ok) {
+        ctx->hog_bf_smem = tensor_hog_bf16_smem(ctx->JP, ctx->hog_bf.max_ev, ctx->hog_bf.max_seg, nF);
+        ctx->hog_bf_grid = std::min<int64_t>(ctx->hog_bf_grid, ctx->hog_bf.ngroups);
+    }
+    // staleness-aware step: a row with kappa updates expected in flight at once takes
+    // gamma / kappa of its step when kappa > gamma (kappa = occurrences x entries in flight
+    // / |Omega|); each HOGWILD grouping stores the scale of every row.  Default gamma =
+    // 320 / (largest rank): 32 at rank 10.  A coupled entry's step has curvature
+    // eta * lambda_m * ||v||^2, which grows with the rank, and gamma stale steps of it must
+    // stay well inside the stable range.
     {
-        const int per_sm = ctx->hog_smem <= kMaxSmem
-                               ? std::max(1, tensor_hog_blocks_per_sm(N, ctx->JP, ctx->hog_smem)) : 1;
-        int64_t cap = (int64_t)per_sm * ctx->num_sms;
-        if (hp->hog_ctas > 0) cap = std::min<int64_t>(cap, hp->hog_ctas);
-        ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(cap, ctx->hog.ngroups));
-        // staleness-aware step: a row with kappa updates expected in flight at once takes
-        // gamma / kappa of its step when kappa > gamma (kappa = occurrences x entries in
-        // flight / |Omega|)
-        const double gamma = hp->hog_staleness == 0.f ? 32.0 : (double)hp->hog_staleness;
-        const double inflight = (double)ctx->hog_grid * (double)tile;
-        for (int F = 0; F < nF; ++F) {
-            std::vector<float> d(occ[(size_t)F].size(), 1.f);
-            if (gamma > 0)
-                for (size_t i = 0; i < d.size(); ++i) {
-                    const double kappa = (double)occ[(size_t)F][i] * inflight / (double)ctx->nnz;
-                    if (kappa > gamma) d[i] = (float)(gamma / kappa);
-                }
-            CK(upload(ctx, &ctx->damp[F], d));
-            ctx->P.damp[F] = ctx->damp[F];
-            CK(cudaStreamSynchronize(ctx->stream));
-        }
+        int jmax = 1;
+        for (int n = 0; n < N; ++n) jmax = std::max(jmax, ctx->J[n]);
+        const double gamma = hp->hog_staleness == 0.f ? 320.0 / jmax : (double)hp->hog_staleness;
+        auto row_scales = [&](DevGrouping& D, double inflight) -> int {
+            for (int F = 0; F < nF; ++F) {
+                std::vector<float> d(occ[(size_t)F].size(), 1.f);
+                if (gamma > 0)
+                    for (size_t i = 0; i < d.size(); ++i) {
+                        const double kappa = (double)occ[(size_t)F][i] * inflight / (double)ctx->nnz;
+                        if (kappa > gamma) d[i] = (float)(gamma / kappa);
+                    }
+                float* p = nullptr;
+                CK(upload(ctx, &p, d));
+                D.d.row_damp[F] = p;
+                CK(cudaStreamSynchronize(ctx->stream));
+            }
+            return S3_OK;
+        };
+        if ((rc = row_scales(ctx->hog, (double)ctx->hog_grid * (double)tile)) != S3_OK) return rc;
+        if (bf16_ok && (rc = row_scales(ctx->hog_bf,
+                                        (double)std::max<int64_t>(ctx->hog_bf_grid, 1) *
+                                            (double)bf_tile)) != S3_OK)
+            return rc;
     }
     // initial parameters
     KL(launch_init_params(ctx->P, ctx->I, ctx->J, ctx->K, ctx->JP, seed, ctx->stream));
@@ -573,32 +652,32 @@ static int enqueue_hogwild(s3_ctx* ctx) {
     const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
     CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
-    KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter,
+    KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->hog_lanes, ctx->P, D.d, D.ngroups, ctx->d_tile_counter,
                          (int)ctx->hog_grid, ctx->d_eta, row_mean,
-                         ctx->hp.core_scale / (float)ctx->hog_grid, D.max_seg, ctx->stream));
+                         ctx->hp.core_scale / (float)ctx->hog_grid, D.max_ev, D.max_seg,
+                         ctx->hog_ccap, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
     return S3_OK;
 }
 
 static int enqueue_hogwild_bf16(s3_ctx* ctx) {
-    DevGrouping& D = ctx->hog;
-    const int nF = ctx->N + ctx->M;
-    if (ctx->N != 3 || ctx->JP != 16)
-        return fail(ctx, S3_ERR_ARG, "the BF16 form is built for 3-way tensors with ranks 11..16");
-    const size_t smem = tensor_hog_bf16_smem(ctx->JP, D.max_seg, nF);
-    if (smem > kMaxSmem)
-        return fail(ctx, S3_ERR_ARG, "a BF16 HOGWILD tile needs " + std::to_string(smem) +
-                                         " bytes of shared memory; lower hog_tile");
+    DevGrouping& D = ctx->hog_bf;
+    if (ctx->N != 3 || (ctx->JP != 16 && ctx->JP != 32))
+        return fail(ctx, S3_ERR_ARG,
+                    "the BF16 form is built for 3-way tensors with ranks 11..16 or 21..32");
+    if (ctx->hog_bf_smem > kMaxSmem)
+        return fail(ctx, S3_ERR_ARG, "a BF16 HOGWILD tile needs " + std::to_string(ctx->hog_bf_smem) +
+                                         " bytes of shared memory (too many coupled entries per tile)");
+    if (ctx->hog_bf_grid < 1)
+        return fail(ctx, S3_ERR_CUDA, "the BF16 HOGWILD kernel cannot be made resident");
     const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
-    int64_t cap = ctx->num_sms;   // one CTA per SM (shared memory and TMEM)
-    if (ctx->hp.hog_ctas > 0) cap = std::min<int64_t>(cap, ctx->hp.hog_ctas);
-    const int grid = (int)std::min<int64_t>(cap, D.ngroups);
+    const int grid = (int)ctx->hog_bf_grid;
     CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     KL(launch_tensor_hog_bf16(ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
-                              ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid, D.max_seg,
-                              ctx->d_kerr, ctx->stream));
+                              ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid, D.max_ev,
+                              D.max_seg, ctx->d_kerr, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
     return S3_OK;
@@ -823,7 +902,10 @@ extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* cons
         for (int n = 0; n < N; ++n) L.contrib[n] = ctx->contrib[n];
         L.core_part = ctx->core_part;
         CK(prof_mark(ctx, S3_K_TENSOR_GRAD));
-        KL(launch_tensor_contrib(N, ctx->JP, ctx->P, D.d, L, ctx->stream));
+        int nparts = 0;
+        KL(launch_tensor_contrib(N, ctx->JP, ctx->P, D.d, L,
+                                 (int)std::min<int64_t>(ctx->core_part_n, 2 * (int64_t)ctx->num_sms),
+                                 &nparts, ctx->stream));
         CK(prof_mark(ctx, S3_K_TENSOR_GRAD));
         prof_count(ctx, S3_K_TENSOR_GRAD, L.e_end - L.e_begin);
         for (int m = 0; m < M; ++m)
@@ -837,12 +919,16 @@ extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* cons
             S.out[F] = outs[F];
             S.comp[F] = ctx->grad_comp + off[F];
             S.Jf[F] = factor_cols(ctx, F);
-            S.seg_begin[F + 1] = S.seg_begin[F] + (D.seg_off[F][(size_t)g + 1] - D.seg_off[F][(size_t)g]);
+            const int64_t ns = D.seg_off[F][(size_t)g + 1] - D.seg_off[F][(size_t)g];
+            S.nlong[F] = D.seg_nlong[F][(size_t)g];
+            S.nhuge[F] = D.seg_nhuge[F][(size_t)g];
+            S.huge_begin[F + 1] = S.huge_begin[F] + S.nhuge[F];
+            S.long_begin[F + 1] = S.long_begin[F] + (S.nlong[F] - S.nhuge[F]);
+            S.short_begin[F + 1] = S.short_begin[F] + (ns - S.nlong[F]);
         }
-        S.total_segs = S.seg_begin[nF];
         KL(launch_segments(ctx->P, D.d, S, ctx->d_eta, 0, 1, ctx->stream));
         const int64_t nt = L.e_end - L.e_begin;
-        KL(launch_core(ctx->P, N, ctx->JP, ctx->J, ctx->core_part, (nt + kTile - 1) / kTile, nt,
+        KL(launch_core(ctx->P, N, ctx->JP, ctx->J, ctx->core_part, nparts, nt,
                        ctx->d_eta, 1.f, 1, dG, ctx->grad_comp, ctx->stream));
     }
     KL(launch_add_comp(dG, ctx->grad_comp, pd, ctx->stream));
@@ -853,6 +939,63 @@ extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* cons
 }
 
 // ------------------------------------------------------------------ params
+// ------------------------------------------------------------------ final QR step
+extern "C" int s3_finalize_qr(s3_ctx* ctx) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    const int N = ctx->N;
+    for (int n = 0; n < N; ++n)
+        if (ctx->I[n] < ctx->J[n])
+            return fail(ctx, S3_ERR_ARG, "s3_finalize_qr: U^(" + std::to_string(n + 1) +
+                                             ") has fewer rows than its rank");
+    // scratch, allocated once: Gram partials, per-mode R and R^-1, pass-1 factors, the flag,
+    // the out-of-place core
+    int64_t grid = 1;
+    for (int n = 0; n < N; ++n) grid = std::max<int64_t>(grid, qr_gram_ctas(ctx->I[n], ctx->num_sms));
+    size_t q = 1;
+    for (int n = 0; n < N - 1; ++n) q *= ctx->JP;
+    const size_t core_n = q * ctx->JPR;
+    if (!ctx->qr_parts) {
+        CK(dalloc(ctx, &ctx->qr_parts, (size_t)grid * 32 * 32));
+        CK(dalloc(ctx, &ctx->qr_R, (size_t)(2 * kMaxN + 2) * 32 * 32));
+        CK(dalloc(ctx, &ctx->qr_bad, (size_t)kMaxN));
+        CK(dalloc(ctx, &ctx->qr_core, core_n));
+        ctx->qr_grid = grid;
+    }
+    double* Rn[kMaxN];
+    double* Rin[kMaxN];
+    for (int n = 0; n < N; ++n) {
+        Rn[n] = ctx->qr_R + (size_t)(2 * n) * 32 * 32;
+        Rin[n] = ctx->qr_R + (size_t)(2 * n + 1) * 32 * 32;
+    }
+    double* R1 = ctx->qr_R + (size_t)(2 * kMaxN) * 32 * 32;
+    double* R1i = R1 + 32 * 32;
+    CK(cudaMemsetAsync(ctx->qr_bad, 0, sizeof(int) * kMaxN, ctx->stream));
+    // every factor first: nothing changes when one of them is rank deficient
+    for (int n = 0; n < N; ++n) {
+        const int g = qr_gram_ctas(ctx->I[n], ctx->num_sms);
+        KL(launch_qr_factor(ctx->P.U[n], ctx->I[n], ctx->JPR, ctx->J[n], std::min<int>(g, (int)ctx->qr_grid),
+                            ctx->qr_parts, Rn[n], Rin[n], R1, R1i, ctx->qr_bad + n, ctx->stream));
+    }
+    int bad[kMaxN] = {};
+    CK(cudaMemcpyAsync(bad, ctx->qr_bad, sizeof(int) * kMaxN, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int n = 0; n < N; ++n)
+        if (bad[n])
+            return fail(ctx, S3_ERR_ARG, "s3_finalize_qr: U^(" + std::to_string(n + 1) +
+                                             ") does not have full column rank");
+    for (int n = 0; n < N; ++n) {
+        KL(launch_qr_rows(ctx->P.U[n], ctx->I[n], ctx->JPR, ctx->J[n], Rin[n], 0, ctx->stream));
+        KL(launch_qr_core(ctx->P.G, ctx->qr_core, N, ctx->JP, ctx->JPR, n, ctx->J[n], Rn[n], ctx->stream));
+        CK(cudaMemcpyAsync(ctx->P.G, ctx->qr_core, core_n * sizeof(float), cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+        for (int m = 0; m < ctx->M; ++m)
+            if (ctx->cmode[m] == n)
+                KL(launch_qr_rows(ctx->P.V[m], ctx->K[m], ctx->JPR, ctx->J[n], Rn[n], 1, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return S3_OK;
+}
+
 extern "C" int s3_get_params(s3_ctx* ctx, float* G, float* const* U, float* const* V) {
     if (!usable(ctx)) return S3_ERR_STATE;
     if (G) KL(launch_unpack_core(G, ctx->P.G, ctx->N, ctx->J, ctx->JP, ctx->stream));
@@ -895,6 +1038,30 @@ extern "C" int s3_info(s3_ctx* ctx, int64_t* n_union, int64_t* n_batches, int64_
     return S3_OK;
 }
 
+extern "C" int s3_hog_config(s3_ctx* ctx, int precision, int64_t* ctas, int64_t* tile,
+                             int64_t* smem_bytes, int64_t* ctas_per_sm) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    int64_t c = 0, tl = 0, sm = 0, per = 0;
+    if (precision == S3_FP32) {
+        c = ctx->hog_grid;
+        tl = ctx->hog_tile;
+        sm = (int64_t)ctx->hog_smem;
+        per = ctx->hog_per_sm;
+    } else if (precision == S3_BF16) {
+        c = ctx->hog_bf_grid;
+        tl = ctx->hog_bf_grid > 0 ? ctx->hog_bf_tile : 0;
+        sm = (int64_t)ctx->hog_bf_smem;
+        per = ctx->hog_bf_per_sm;
+    } else {
+        return fail(ctx, S3_ERR_ARG, "precision must be S3_FP32 or S3_BF16");
+    }
+    if (ctas) *ctas = c;
+    if (tile) *tile = tl;
+    if (smem_bytes) *smem_bytes = sm;
+    if (ctas_per_sm) *ctas_per_sm = per;
+    return S3_OK;
+}
+
 // ------------------------------------------------------------------ values from the host
 extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val) {
     if (!usable(ctx)) return S3_ERR_STATE;
@@ -903,16 +1070,20 @@ extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* co
     for (int m = 0; m < ctx->M; ++m) total += ctx->ynnz[m];
     if (!ctx->values_stage) CK(dalloc(ctx, &ctx->values_stage, (size_t)total));
     CK(cudaMemcpyAsync(ctx->values_stage, x_val, (size_t)ctx->nnz * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    DevGrouping* gs[3] = {&ctx->mb, &ctx->hog, &ctx->grad};
+    DevGrouping* gs[4] = {&ctx->mb, &ctx->hog, &ctx->grad, &ctx->hog_bf};
+    // groupings that were not built for this context (ngroups 0) hold no arrays
     for (DevGrouping* D : gs)
-        KL(launch_gather_f32(D->tval, ctx->values_stage, D->t_src, D->t_off.back(), ctx->stream));
+        if (D->ngroups > 0)
+            KL(launch_gather_f32(D->tval, ctx->values_stage, D->t_src, D->t_off.back(), ctx->stream));
     int64_t o = ctx->nnz;
     for (int m = 0; m < ctx->M; ++m) {
         if (y_val && y_val[m]) {
             CK(cudaMemcpyAsync(ctx->values_stage + o, y_val[m], (size_t)ctx->ynnz[m] * sizeof(float),
                                cudaMemcpyHostToDevice, ctx->stream));
             for (DevGrouping* D : gs)
-                KL(launch_gather_f32(D->cval[m], ctx->values_stage + o, D->c_src[m], ctx->ynnz[m], ctx->stream));
+                if (D->ngroups > 0)
+                    KL(launch_gather_f32(D->cval[m], ctx->values_stage + o, D->c_src[m], ctx->ynnz[m],
+                                         ctx->stream));
         }
         o += ctx->ynnz[m];
     }

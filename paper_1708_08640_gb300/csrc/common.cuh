@@ -19,7 +19,6 @@ struct DParams {
     float* V[kMaxM];
     const float* inv_cnt[kMaxF];   // 1/|Omega^{n,i}| for factor n, 1/|Omega_Y^{2,k}| for
                                    // factor N+m; 0 for rows without observed entries
-    const float* damp[kMaxF];      // HOGWILD step scale of each row (staleness-aware)
     int ld;                        // row stride (floats) of every factor matrix
     int ldg;                       // row stride (floats) of the padded core's last mode
     int N, M;
@@ -32,6 +31,11 @@ struct DParams {
 // group's occurrences ("events") of rows are sorted by row into segments; `tpos`/`cpos_*`
 // give an event's local slot (position among the group's sorted events of that factor) or
 // local segment, depending on the grouping's kind.
+// Segments of up to kShortSeg events are summed by one thread, longer ones by a warp, and
+// (where a grouping marks them) those of more than kHugeSeg events by a whole CTA.
+constexpr int kShortSeg = 16;
+constexpr int kHugeSeg = 1024;
+
 struct DGroup {
     const int64_t* t_off;
     const int32_t* tidx[kMaxN];
@@ -47,7 +51,11 @@ struct DGroup {
     const int32_t* seg_row[kMaxF];     // row of each segment
     const int32_t* seg_start[kMaxF];   // local slot of the segment's first event
     const int32_t* seg_cnt[kMaxF];     // events in the segment
+    const int32_t* seg_nlong[kMaxF];   // [groups] segments of more than kShortSeg events, which
+                                       // come first in their group (slot-positioned groupings)
     const int64_t* slot_off[kMaxF];    // [groups + 1] global slot range of each group
+    const float* row_damp[kMaxF];      // HOGWILD groupings: step scale of every row of each
+                                       // factor (the staleness-aware step), else null
 };
 
 __host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
@@ -80,5 +88,42 @@ struct Kahan {
     }
     __device__ __forceinline__ float value() const { return s + c; }
 };
+
+// Compensated sums, component by component, of the rows src + e * ld (4 * C4 floats each,
+// 16-byte aligned) for e = e0, e0 + step, ... < cnt, added in that order; several rows'
+// loads are in flight at once.
+template <int C4>
+__device__ __forceinline__ void rows_sum(const float* src, int64_t ld, int e0, int step, int cnt,
+                                         Kahan (&k)[4 * C4]) {
+    constexpr int U = C4 <= 4 ? 4 : 2;
+    int e = e0;
+    for (; e + (U - 1) * step < cnt; e += U * step) {
+        float4 v[U][C4];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < C4; ++q)
+                v[u][q] = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)(e + u * step) * ld + 4 * q));
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < C4; ++q) {
+                k[4 * q].add(v[u][q].x);
+                k[4 * q + 1].add(v[u][q].y);
+                k[4 * q + 2].add(v[u][q].z);
+                k[4 * q + 3].add(v[u][q].w);
+            }
+    }
+    for (; e < cnt; e += step) {
+#pragma unroll
+        for (int q = 0; q < C4; ++q) {
+            const float4 v = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)e * ld + 4 * q));
+            k[4 * q].add(v.x);
+            k[4 * q + 1].add(v.y);
+            k[4 * q + 2].add(v.z);
+            k[4 * q + 3].add(v.w);
+        }
+    }
+}
 
 }  // namespace s3

@@ -1,39 +1,69 @@
 // Per-tile bookkeeping shared by the HOGWILD kernels (FP32 and BF16 forms): the tile's row
-// accumulators in shared memory, its coupled-matrix entries, and the final row steps.
+// gradient slots in shared memory, its coupled-matrix entries, and the final row steps.
 #pragma once
 #include "common.cuh"
 #include "tensor_fp32.cuh"
 
 namespace s3 {
 
-// per-factor offsets (floats) of the HOGWILD row accumulators in shared memory
+// A tile's row gradients go to slots in shared memory, one slot per event (the grouping
+// numbers a group's events of every factor in row order, so the events of one row occupy
+// consecutive slots); the flush sums each row's slots in slot order.  No shared-memory
+// atomics, and a fixed summation order inside the tile.
+//
+// The FP32 kernel's prefetch warp loads, one tile ahead, everything a tile reads besides the
+// parameters into one of two metadata buffers (HogMeta): the tile index, its tensor entries'
+// indices, values and slot positions, its coupled entries and its segment table.  Offsets
+// inside a buffer, in 4-byte words:
+struct HogMeta {
+    int tidx;           // [N][ST] row indices of the tile's tensor entries
+    int tpos;           // [N][ST] their slot positions
+    int tval;           // [ST] their values
+    int c_r, c_k, c_pu, c_pv, c_y, c_m;   // [ccap] coupled entries: row, column, slots, value,
+                                          // matrix (all matrices of the tile in order)
+    int tab[kMaxF];     // [max_seg[F]] x 16 bytes: segment table of factor F
+    int size;           // words per buffer (a multiple of 4)
+};
+// header words of a metadata buffer
+constexpr int kMetaTile = 0;    // tile index (int64 in words 0-1)
+constexpr int kMetaNb = 2;      // tensor entries
+constexpr int kMetaNc = 3;      // coupled entries (all matrices)
+constexpr int kMetaNseg = 4;    // [kMaxF] segments per factor
+constexpr int kMetaHeader = 16; // words (4 + kMaxF)
+
 struct HogSmem {
-    int off[kMaxF];
+    int off[kMaxF];    // per-factor offset (floats) of the slot rows in dynamic shared memory
+    int toff[kMaxF];   // per-factor offset (floats) of the tile's segment table (BF16 kernel)
+    int noff;          // offset (floats) of the tile's segment counts (kMaxF ints; BF16 kernel)
     int nF;
+    int meta[2];       // FP32 kernel: offsets (words) of the two metadata buffers
+    HogMeta M;
 };
 
-// zero the accumulators of tile t's segments
+// Floats per slot row.  Rows are written with 16-byte stores, which a warp issues in phases
+// of 8 lanes; an odd number of 16-byte units per row puts the 8 lanes' rows on distinct banks.
+__host__ __device__ constexpr int slot_stride(int JPR) { return (JPR / 4) % 2 ? JPR : JPR + 4; }
+
+// one gradient row (JPR values, zero padding included) into its slot
 template <int JPR>
-__device__ __forceinline__ void hog_clear(float* smem, const DGroup& Gr, int64_t t, const HogSmem& H) {
-    for (int F = 0; F < H.nF; ++F) {
-        const int nseg = (int)(Gr.seg_off[F][t + 1] - Gr.seg_off[F][t]);
-        float* sa = smem + H.off[F];
-        for (int l = threadIdx.x * 4; l < nseg * JPR; l += blockDim.x * 4)
-            st4(sa + l, make_float4(0, 0, 0, 0));
-    }
+__device__ __forceinline__ void put_slot(float* smem, const HogSmem& H, int F, int32_t slot,
+                                         const float (&c)[JPR]) {
+    float* d = smem + H.off[F] + slot * slot_stride(JPR);
+#pragma unroll
+    for (int q = 0; q < JPR / 4; ++q) st4(d + 4 * q, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
 }
 
-// Eq. (8), coupled rows, for the coupled entries of tile t: read the current rows, add the
-// gradients into the tile's accumulators (shared-memory atomics)
+// Eq. (8), coupled rows, for the coupled entries of tile t: read the current rows and write
+// the gradients to their slots.  Threads first, first + stride, ... take the entries.
 template <int JP>
 __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, int64_t t,
-                                            float* smem, const HogSmem& H) {
+                                            float* smem, const HogSmem& H, int first, int stride) {
     constexpr int JPR = round4(JP);
     for (int m = 0; m < P.M; ++m) {
         const int c = P.cmode[m];
         const int64_t c0 = Gr.c_off[m][t], c1 = Gr.c_off[m][t + 1];
         const float lm = P.lambda_m;
-        for (int64_t e = c0 + threadIdx.x; e < c1; e += blockDim.x) {
+        for (int64_t e = c0 + first; e < c1; e += stride) {
             const int32_t r = __ldg(Gr.cr[m] + e), k = __ldg(Gr.cc[m] + e);
             float u[JP], v[JP];
             load_row<JP, true>(P.U[c] + (int64_t)r * JPR, u);
@@ -43,37 +73,231 @@ __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, 
             for (int j = 0; j < JP; ++j) yh = fmaf(u[j], v[j], yh);
             const float err = __ldg(Gr.cval[m] + e) - yh;
             const float rv = lm * P.lambda_reg * __ldg(P.inv_cnt[P.N + m] + k);
-            float* su = smem + H.off[c] + __ldg(Gr.cpos_u[m] + e) * JPR;
-            float* sv = smem + H.off[P.N + m] + __ldg(Gr.cpos_v[m] + e) * JPR;
+            float du[JPR], dv[JPR];
 #pragma unroll
-            for (int j = 0; j < JP; ++j) {
-                atomicAdd(su + j, -lm * err * v[j]);
-                atomicAdd(sv + j, fmaf(-lm * err, u[j], rv * v[j]));
+            for (int j = 0; j < JPR; ++j) {
+                du[j] = j < JP ? -lm * err * v[j] : 0.f;
+                dv[j] = j < JP ? fmaf(-lm * err, u[j], rv * v[j]) : 0.f;
             }
+            put_slot<JPR>(smem, H, c, __ldg(Gr.cpos_u[m] + e), du);
+            put_slot<JPR>(smem, H, P.N + m, __ldg(Gr.cpos_v[m] + e), dv);
         }
     }
 }
 
-// apply tile t's row steps: one vector atomic per 4 values of every touched row,
-// step = -eta * damp[row] * (sum or mean of the row's gradients in the tile)
-template <int JPR>
-__device__ __forceinline__ void hog_flush(const DParams& P, const DGroup& Gr, int64_t t,
-                                          const float* smem, const HogSmem& H, float eta,
-                                          int row_mean) {
+// Tile t's segment table, per factor and segment: (row, first slot, events, step scale),
+// 16 bytes, in shared memory, with the segment counts; loaded in the tile's prologue so
+// that the flush needs no global round trip.  Threads first, first + stride, ... take part.
+// Ends without a barrier.
+__device__ __forceinline__ void hog_tables(const DGroup& Gr, int64_t t, float* smem,
+                                           const HogSmem& H, int first, int stride) {
+    int* cnts = reinterpret_cast<int*>(smem + H.noff);
     for (int F = 0; F < H.nF; ++F) {
-        const int64_t sg0 = Gr.seg_off[F][t];
-        const int nseg = (int)(Gr.seg_off[F][t + 1] - sg0);
+        const int64_t s0 = Gr.seg_off[F][t];
+        const int ns = (int)(Gr.seg_off[F][t + 1] - s0);
+        if (first == 0) cnts[F] = ns;
+        int4* tab = reinterpret_cast<int4*>(smem + H.toff[F]);
+        for (int l = first; l < ns; l += stride) {
+            const int32_t row = __ldg(Gr.seg_row[F] + s0 + l);
+            tab[l] = make_int4(row, __ldg(Gr.seg_start[F] + s0 + l), __ldg(Gr.seg_cnt[F] + s0 + l),
+                               __float_as_int(__ldg(Gr.row_damp[F] + row)));
+        }
+    }
+}
+
+// Eq. (8), coupled rows, for one coupled entry of matrix m (row u of U^(c), column k of
+// V_m, value y) whose rows were gathered already: the gradients to slots pu and pv
+template <int JP>
+__device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, const HogSmem& H,
+                                                int m, int k, int32_t pu, int32_t pv, float y,
+                                                const float (&u)[JP], const float (&v)[JP]) {
+    constexpr int JPR = round4(JP);
+    float yh = 0.f;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) yh = fmaf(u[j], v[j], yh);
+    const float lm = P.lambda_m;
+    const float err = y - yh;
+    const float rv = lm * P.lambda_reg * __ldg(P.inv_cnt[P.N + m] + k);
+    float du[JPR], dv[JPR];
+#pragma unroll
+    for (int j = 0; j < JPR; ++j) {
+        du[j] = j < JP ? -lm * err * v[j] : 0.f;
+        dv[j] = j < JP ? fmaf(-lm * err, u[j], rv * v[j]) : 0.f;
+    }
+    put_slot<JPR>(smem, H, P.cmode[m], pu, du);
+    put_slot<JPR>(smem, H, P.N + m, pv, dv);
+}
+
+// apply tile t's row steps: per touched row and 4 components, the sum of its slots in slot
+// order, then one vector atomic, step = -eta * (step scale of the row) * (sum or mean of the
+// row's gradients in the tile)
+template <int JPR>
+__device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, const HogSmem& H,
+                                          float eta, int row_mean) {
+    constexpr int SS = slot_stride(JPR);
+    const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
+    for (int F = 0; F < H.nF; ++F) {
+        const int nseg = cnts[F];
         const float* sa = smem + H.off[F];
+        const int4* tab = reinterpret_cast<const int4*>(smem + H.toff[F]);
         float* base = F < P.N ? P.U[F] : P.V[F - P.N];
         for (int l = threadIdx.x; l < nseg * (JPR / 4); l += blockDim.x) {
             const int s = l / (JPR / 4), q = l % (JPR / 4);
-            const int32_t rr = __ldg(Gr.seg_row[F] + sg0 + s);
-            const float den = row_mean ? (float)__ldg(Gr.seg_cnt[F] + sg0 + s) : 1.f;
-            const float sc = -eta * __ldg(P.damp[F] + rr) / den;
-            const float4 v = *reinterpret_cast<const float4*>(sa + s * JPR + 4 * q);
-            red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * v.x, sc * v.y, sc * v.z, sc * v.w);
+            const int4 sg = tab[s];   // row, first slot, events, step scale
+            const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
+            float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
+            for (int k = 1; k < cnt; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(sa + (st + k) * SS + 4 * q);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+            const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
+            red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
         }
     }
+}
+
+// The prefetch warp's part: tile t's metadata into the buffer at meta (see HogMeta).  Only
+// the writing lanes touch the buffer; the CTA barrier that follows publishes it.
+// t >= n_tiles writes only the tile index (the CTA stops there).
+template <int N>
+__device__ __forceinline__ void hog_prefetch(const DParams& P, const DGroup& Gr, int64_t t,
+                                             int64_t n_tiles, int* meta, const HogSmem& H,
+                                             int ST, int lane) {
+    if (lane == 0) *reinterpret_cast<int64_t*>(meta + kMetaTile) = t;
+    if (t >= n_tiles) return;
+    const HogMeta& M = H.M;
+    const int64_t e0 = Gr.t_off[t];
+    const int nb = (int)(Gr.t_off[t + 1] - e0);
+    for (int l = lane; l < nb; l += 32) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            meta[M.tidx + n * ST + l] = __ldg(Gr.tidx[n] + e0 + l);
+            meta[M.tpos + n * ST + l] = __ldg(Gr.tpos[n] + e0 + l);
+        }
+        meta[M.tval + l] = __float_as_int(__ldg(Gr.tval + e0 + l));
+    }
+    int nc = 0;
+    for (int m = 0; m < P.M; ++m) {
+        const int64_t c0 = Gr.c_off[m][t];
+        const int n = (int)(Gr.c_off[m][t + 1] - c0);
+        for (int l = lane; l < n; l += 32) {
+            const int w = nc + l;
+            meta[M.c_r + w] = __ldg(Gr.cr[m] + c0 + l);
+            meta[M.c_k + w] = __ldg(Gr.cc[m] + c0 + l);
+            meta[M.c_pu + w] = __ldg(Gr.cpos_u[m] + c0 + l);
+            meta[M.c_pv + w] = __ldg(Gr.cpos_v[m] + c0 + l);
+            meta[M.c_y + w] = __float_as_int(__ldg(Gr.cval[m] + c0 + l));
+            meta[M.c_m + w] = m;
+        }
+        nc += n;
+    }
+    for (int F = 0; F < H.nF; ++F) {
+        const int64_t s0 = Gr.seg_off[F][t];
+        const int ns = (int)(Gr.seg_off[F][t + 1] - s0);
+        if (lane == 0) meta[kMetaNseg + F] = ns;
+        int4* tab = reinterpret_cast<int4*>(meta + M.tab[F]);
+        for (int l = lane; l < ns; l += 32) {
+            const int32_t row = __ldg(Gr.seg_row[F] + s0 + l);
+            tab[l] = make_int4(row, __ldg(Gr.seg_start[F] + s0 + l), __ldg(Gr.seg_cnt[F] + s0 + l),
+                               __float_as_int(__ldg(Gr.row_damp[F] + row)));
+        }
+    }
+    if (lane == 0) {
+        meta[kMetaNb] = nb;
+        meta[kMetaNc] = nc;
+    }
+}
+
+// hog_flush over the segment table of a metadata buffer; threads first, first + stride, ...
+template <int JPR>
+__device__ __forceinline__ void hog_flush_meta(const DParams& P, const float* smem, const HogSmem& H,
+                                               const int* meta, float eta, int row_mean, int first,
+                                               int stride) {
+    constexpr int SS = slot_stride(JPR);
+    for (int F = 0; F < H.nF; ++F) {
+        const int nseg = meta[kMetaNseg + F];
+        const float* sa = smem + H.off[F];
+        const int4* tab = reinterpret_cast<const int4*>(meta + H.M.tab[F]);
+        float* base = F < P.N ? P.U[F] : P.V[F - P.N];
+        for (int l = first; l < nseg * (JPR / 4); l += stride) {
+            const int s = l / (JPR / 4), q = l % (JPR / 4);
+            const int4 sg = tab[s];   // row, first slot, events, step scale
+            const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
+            float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
+            for (int k = 1; k < cnt; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(sa + (st + k) * SS + 4 * q);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+            const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
+            red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+        }
+    }
+}
+
+// Layout of the FP32 kernel's shared memory after base_floats (the core copies and the
+// stage): slot rows of every factor, then the two metadata buffers (ST tensor entries and
+// ccap coupled entries at most per tile).  Returns the total in floats.
+__host__ inline size_t hog_meta_smem_floats(int JPR, int N, int ST, const int64_t* max_events,
+                                            const int64_t* max_segs, int64_t ccap, int nF,
+                                            HogSmem* H, size_t base_floats) {
+    size_t off = base_floats;
+    for (int F = 0; F < nF; ++F) {
+        if (H) H->off[F] = (int)off;
+        off += (size_t)max_events[F] * slot_stride(JPR);
+    }
+    HogMeta M{};
+    size_t w = kMetaHeader;
+    M.tidx = (int)w; w += (size_t)N * ST;
+    M.tpos = (int)w; w += (size_t)N * ST;
+    M.tval = (int)w; w += (size_t)ST;
+    M.c_r = (int)w; w += (size_t)ccap;
+    M.c_k = (int)w; w += (size_t)ccap;
+    M.c_pu = (int)w; w += (size_t)ccap;
+    M.c_pv = (int)w; w += (size_t)ccap;
+    M.c_y = (int)w; w += (size_t)ccap;
+    M.c_m = (int)w; w += (size_t)ccap;
+    w = (w + 3) & ~(size_t)3;
+    for (int F = 0; F < kMaxF; ++F) {
+        M.tab[F] = (int)w;
+        if (F < nF) w += (size_t)max_segs[F] * 4;
+    }
+    M.size = (int)((w + 3) & ~(size_t)3);
+    if (H) {
+        H->M = M;
+        H->meta[0] = (int)off;
+        H->meta[1] = (int)(off + M.size);
+        H->nF = nF;
+        H->noff = 0;
+        for (int F = 0; F < kMaxF; ++F) H->toff[F] = 0;
+    }
+    return off + 2 * (size_t)M.size;
+}
+
+// Shared-memory layout after base_floats: every factor's slot rows (max_events[F] rows),
+// then its segment table (max_segs[F] x 16 bytes), then the kMaxF segment counts; each area
+// 16-byte aligned.  Returns the total in floats.
+__host__ inline size_t hog_smem_floats(int JPR, const int64_t* max_events, const int64_t* max_segs,
+                                       int nF, HogSmem* H, size_t base_floats) {
+    size_t off = base_floats;
+    for (int F = 0; F < nF; ++F) {
+        if (H) H->off[F] = (int)off;
+        off += (size_t)max_events[F] * slot_stride(JPR);
+    }
+    for (int F = 0; F < nF; ++F) {
+        if (H) H->toff[F] = (int)off;
+        off += (size_t)max_segs[F] * 4;
+    }
+    if (H) H->noff = (int)off;
+    off += kMaxF;
+    off = (off + 3) & ~(size_t)3;
+    if (H) H->nF = nF;
+    return off;
 }
 
 }  // namespace s3

@@ -1,12 +1,13 @@
 // The deterministic minibatch epoch as one cooperative launch (sm_103a, FP32 form).
 //
 // Every batch of the visiting order takes two phases separated by grid-wide barriers:
-//   A  the batch's tensor entries (spread over all CTAs, one per thread) and coupled entries
-//      compute their Eq. (8) row gradients at the batch-start parameters and write them to
-//      their segment slots; each CTA writes its partial of sum_b e_b a1 o .. o aN;
-//   B  one warp per touched row sums the row's slots in slot order (compensated) and applies
-//      the row step; one warp per core element sums the CTA partials in CTA order and
-//      applies the core step.
+//   A  the batch's tensor entries (chunks of 32 to 256 entries, one chunk per CTA) and
+//      coupled entries (spread over the other CTAs) compute their Eq. (8) row gradients at
+//      the batch-start parameters and write them to their segment slots; each CTA with a
+//      tensor chunk writes its partial of sum_b e_b a1 o .. o aN;
+//   B  one thread per short segment, or one warp per long one, sums a touched row's slots in
+//      slot order (compensated) and applies the row step; one warp per core element sums
+//      the CTA partials in CTA order and applies the core step.
 // The slot layout, the sums' order and the CTA partitioning are fixed, so the epoch is
 // deterministic.  Parameters change inside the launch, so every parameter read is a
 // coherent (L2) load.  The barrier waits are bounded: after ~1 s without progress a CTA sets
@@ -52,6 +53,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int
     return *s_ok != 0;
 }
 
+// entries of a phase-A chunk at most: two lanes per entry for 3-way tensors, one for 4-way
+__host__ __device__ constexpr int mb_stage_rows(int N) { return N == 3 ? kTile / 2 : kTile; }
+
 struct MbArgs {
     float* contrib[kMaxF];
     float* core_part;       // gridDim.x partials of JP^N floats
@@ -69,6 +73,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
     constexpr int JPR = round4(JP);
     constexpr int Q = ipow_t<JP, N - 1>::v;
     constexpr int Pd = Q * JP;
+    constexpr int ST = mb_stage_rows(N);   // entries per chunk at most: rows per stage block
     extern __shared__ __align__(16) float smem[];
     __shared__ int s_ok;
     float* sG = smem;
@@ -81,46 +86,132 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
     for (int64_t b = 0; b < A.n_batches; ++b) {
         // ------------------------------------------------ phase A: gradients into slots
         for (int l = tid * 4; l < Q * JPR; l += kTile * 4) st4(sG + l, ld4_cg(P.G + l));
+        // tensor entries in chunks of 32..kChunkEntries (spread over the CTAs, at least 32
+        // per chunk), chunk c on CTA c mod grid: only the first n_part CTAs hold a core
+        // partial, which keeps phase B's core sums short
         const int64_t t0 = Gr.t_off[b], t1 = Gr.t_off[b + 1];
-        const int64_t per = (t1 - t0 + gridDim.x - 1) / gridDim.x;
-        const int64_t my0 = t0 + (int64_t)blockIdx.x * per;
-        const int nb = (int)max((int64_t)0, min(per, t1 - my0));
+        constexpr int kChunkEntries = ST;
+        const int64_t chunk = min((int64_t)kChunkEntries,
+                                  max((int64_t)32, (t1 - t0 + gridDim.x - 1) / gridDim.x));
+        const int64_t n_chunks = (t1 - t0 + chunk - 1) / chunk;
+        const int n_part = (int)min(n_chunks, (int64_t)gridDim.x);
+        CoreAcc<N, JP, ST> acc;
+        acc.init();
         __syncthreads();
-        if (tid < nb) {
-            const int64_t e = my0 + tid;
-            float a[N][JP];
-            int32_t row[N];
+        for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
+            const int64_t my0 = t0 + ch * chunk;
+            const int nb = (int)min(chunk, t1 - my0);
+            if constexpr (N == 3) {
+                // two lanes per entry (halves each entry's latency); invalid slots run on zeros so
+                // that every lane takes part in the shuffles
+                constexpr int L = 2;
+                constexpr int JH = (JP + L - 1) / L;
+                const int slot = tid / L, lsub = tid % L;
+                const bool valid = slot < nb;
+                const int64_t e = my0 + (valid ? slot : 0);
+                int32_t row[3] = {0, 0, 0};
+                float a1s[JH], a2[JP], a3[JP];
+                float x = 0.f;
+                const int j1base = lsub * JH;
+                if (valid) {
 #pragma unroll
-            for (int n = 0; n < N; ++n) {
-                row[n] = __ldg(Gr.tidx[n] + e);
-                load_row<JP, true>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
+                    for (int n = 0; n < 3; ++n) row[n] = __ldg(Gr.tidx[n] + e);
+                    const float* u1 = P.U[0] + (int64_t)row[0] * JPR;
+#pragma unroll
+                    for (int jj = 0; jj < JH; ++jj) a1s[jj] = j1base + jj < JP ? __ldcg(u1 + j1base + jj) : 0.f;
+                    load_row<JP, true>(P.U[1] + (int64_t)row[1] * JPR, a2);
+                    load_row<JP, true>(P.U[2] + (int64_t)row[2] * JPR, a3);
+                    x = __ldg(Gr.tval + e);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < JH; ++jj) a1s[jj] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < JP; ++j) { a2[j] = 0.f; a3[j] = 0.f; }
+                }
+                float p1s[JH], p2[JP], p3[JP];
+                float xt = partials3_lane<JP, L>(sG, j1base, a1s, a2, a3, p1s, p2, p3);
+                xt += __shfl_xor_sync(0xffffffffu, xt, 1);
+#pragma unroll
+                for (int j = 0; j < JP; ++j) {
+                    p2[j] += __shfl_xor_sync(0xffffffffu, p2[j], 1);
+                    p3[j] += __shfl_xor_sync(0xffffffffu, p3[j], 1);
+                }
+                if (valid) {
+                    const float err = x - xt;
+                    // mode 1: this lane's j1 values (its slot holds all JPR components: the two
+                    // lanes write disjoint ones, the padding is written by lane 1)
+                    const float r1 = P.lambda_reg * __ldg(P.inv_cnt[0] + row[0]);
+                    float* d1 = A.contrib[0] + (int64_t)__ldg(Gr.tpos[0] + e) * JPR;
+                    float* sp1 = stage + (0 * ST + slot) * JPR;
+#pragma unroll
+                    for (int jj = 0; jj < JH; ++jj) {
+                        const int j1 = j1base + jj;
+                        if (j1 < JP) {
+                            d1[j1] = fmaf(-err, p1s[jj], r1 * a1s[jj]);
+                            sp1[j1] = err * a1s[jj];
+                        }
+                    }
+                    if (lsub == L - 1)
+                        for (int j = JP; j < JPR; ++j) d1[j] = 0.f;
+                    // modes 2 and 3: each lane writes the whole slot of one mode
+                    // (element-wise selects keep p2, p3, a2, a3 in registers)
+                    const int n = 1 + lsub;
+                    const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                    float c[JPR];
+                    float* sp = stage + (n * ST + slot) * JPR;
+#pragma unroll
+                    for (int j = 0; j < JPR; ++j) {
+                        const float pj = lsub == 0 ? p2[j < JP ? j : 0] : p3[j < JP ? j : 0];
+                        const float aj = lsub == 0 ? a2[j < JP ? j : 0] : a3[j < JP ? j : 0];
+                        c[j] = j < JP ? fmaf(-err, pj, r * aj) : 0.f;
+                        if (j < JP) sp[j] = aj;
+                    }
+                    float* dst = A.contrib[n] + (int64_t)__ldg(Gr.tpos[n] + e) * JPR;
+#pragma unroll
+                    for (int q = 0; q < JPR / 4; ++q)
+                        st4(dst + 4 * q, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
+                }
+            } else if (tid < nb) {
+                const int64_t e = my0 + tid;
+                float a[N][JP];
+                int32_t row[N];
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    row[n] = __ldg(Gr.tidx[n] + e);
+                    load_row<JP, true>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
+                }
+                float p[N][JP];
+                const float xt = partials4<JP>(sG, a[0], a[1], a[2], a[3], p[0], p[1], p[2], p[3]);
+                const float err = __ldg(Gr.tval + e) - xt;
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                    float c[JPR];
+#pragma unroll
+                    for (int j = 0; j < JPR; ++j) c[j] = j < JP ? fmaf(-err, p[n][j], r * a[n][j]) : 0.f;
+                    float* dst = A.contrib[n] + (int64_t)__ldg(Gr.tpos[n] + e) * JPR;
+#pragma unroll
+                    for (int q = 0; q < JPR / 4; ++q)
+                        st4(dst + 4 * q, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
+                    float* sp = stage + (n * ST + tid) * JPR;
+#pragma unroll
+                    for (int j = 0; j < JP; ++j) sp[j] = n == 0 ? err * a[n][j] : a[n][j];
+                }
             }
-            float p[N][JP];
-            float xt;
-            if constexpr (N == 3) xt = partials3<JP>(sG, a[0], a[1], a[2], p[0], p[1], p[2]);
-            else xt = partials4<JP>(sG, a[0], a[1], a[2], a[3], p[0], p[1], p[2], p[3]);
-            const float err = __ldg(Gr.tval + e) - xt;
-#pragma unroll
-            for (int n = 0; n < N; ++n) {
-                const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
-                float c[JPR];
-#pragma unroll
-                for (int j = 0; j < JPR; ++j) c[j] = j < JP ? fmaf(-err, p[n][j], r * a[n][j]) : 0.f;
-                float* dst = A.contrib[n] + (int64_t)__ldg(Gr.tpos[n] + e) * JPR;
-#pragma unroll
-                for (int q = 0; q < JPR / 4; ++q)
-                    st4(dst + 4 * q, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
-                float* sp = stage + (n * kTile + tid) * JPR;
-#pragma unroll
-                for (int j = 0; j < JP; ++j) sp[j] = n == 0 ? err * a[n][j] : a[n][j];
-            }
+            __syncthreads();
+            acc.add_tile(stage, nb);
+            __syncthreads();
         }
-        // coupled entries of the batch, spread the same way
-        for (int m = 0; m < P.M; ++m) {
+        // coupled entries of the batch, spread evenly over the CTAs without a tensor chunk
+        // (over all CTAs when every one has one)
+        const int c_first = n_part < (int)gridDim.x ? n_part : 0;
+        const int c_ctas = (int)gridDim.x - c_first;
+        const int c_me = (int)blockIdx.x - c_first;
+        for (int m = 0; m < P.M && c_me >= 0; ++m) {
             const int c = P.cmode[m];
             const int64_t c0 = Gr.c_off[m][b], c1 = Gr.c_off[m][b + 1];
-            const int64_t cper = (c1 - c0 + gridDim.x - 1) / gridDim.x;
-            const int64_t cm0 = c0 + (int64_t)blockIdx.x * cper;
+            const int64_t cper = (c1 - c0 + c_ctas - 1) / c_ctas;
+            const int64_t cm0 = c0 + (int64_t)c_me * cper;
             const int64_t cm1 = min(c1, cm0 + cper);
             for (int64_t e = cm0 + tid; e < cm1; e += kTile) {
                 const int32_t r = __ldg(Gr.cr[m] + e), k = __ldg(Gr.cc[m] + e);
@@ -147,60 +238,73 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                 }
             }
         }
-        __syncthreads();
-        {
-            CoreAcc<N, JP> acc;
-            acc.init();
-            acc.add_tile(stage, nb);
-            __syncthreads();
-            acc.store(A.core_part + (int64_t)blockIdx.x * Pd, stage);
-        }
+        if ((int)blockIdx.x < n_part) acc.store(A.core_part + (int64_t)blockIdx.x * Pd, stage);
         if (!grid_barrier(A.bar_count, A.bar_gen, &s_ok)) break;
         // ------------------------------------------------ phase B: ordered sums and steps
-        int64_t seg_begin[kMaxF + 1];
-        seg_begin[0] = 0;
-        for (int F = 0; F < nF; ++F)
-            seg_begin[F + 1] = seg_begin[F] + (Gr.seg_off[F][b + 1] - Gr.seg_off[F][b]);
-        const int64_t n_seg = seg_begin[nF];
-        const int64_t n_items = n_seg + Pd;
-        const int64_t gwarp = ((int64_t)blockIdx.x * kTile + tid) >> 5;
-        const int64_t nwarps = ((int64_t)gridDim.x * kTile) >> 5;
+        // each group lists its long segments (more than kShortSeg events) first
+        int64_t long_begin[kMaxF + 1], short_begin[kMaxF + 1];
+        int32_t nlong[kMaxF];
+        long_begin[0] = short_begin[0] = 0;
+        for (int F = 0; F < nF; ++F) {
+            nlong[F] = __ldg(Gr.seg_nlong[F] + b);
+            long_begin[F + 1] = long_begin[F] + nlong[F];
+            short_begin[F + 1] = short_begin[F] + (Gr.seg_off[F][b + 1] - Gr.seg_off[F][b]) - nlong[F];
+        }
+        const int64_t n_short = short_begin[nF], n_long = long_begin[nF];
+        const int64_t gthread = (int64_t)blockIdx.x * kTile + tid;
+        const int64_t nthreads = (int64_t)gridDim.x * kTile;
+        // pass 1: a thread per short segment (the common case: rows touched a few times)
+        for (int64_t w = gthread; w < n_short; w += nthreads) {
+            int F = 0;
+            while (F + 1 < nF && w >= short_begin[F + 1]) ++F;
+            const int64_t sg = Gr.seg_off[F][b] + nlong[F] + (w - short_begin[F]);
+            const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
+            const int32_t row = __ldg(Gr.seg_row[F] + sg);
+            const int32_t st = __ldg(Gr.seg_start[F] + sg);
+            const float* src = A.contrib[F] + (int64_t)st * JPR;
+            const float sc = -eta / (A.row_mean ? (float)cnt : 1.f);
+            float* base = (F < P.N ? P.U[F] : P.V[F - P.N]) + (int64_t)row * JPR;
+            Kahan k[JPR];
+#pragma unroll
+            for (int j = 0; j < JPR; ++j) k[j].init();
+            rows_sum<JPR / 4>(src, JPR, 0, 1, cnt, k);
+#pragma unroll
+            for (int q = 0; q < JPR / 4; ++q) {
+                float4 u = ld4_cg(base + 4 * q);
+                u.x = fmaf(sc, k[4 * q].value(), u.x);
+                u.y = fmaf(sc, k[4 * q + 1].value(), u.y);
+                u.z = fmaf(sc, k[4 * q + 2].value(), u.z);
+                u.w = fmaf(sc, k[4 * q + 3].value(), u.w);
+                st4(base + 4 * q, u);
+            }
+        }
+        // pass 2: a warp per long segment and per core element
+        // (the core elements first: every batch has them, and their warps start at once)
+        const int64_t n_items = Pd + n_long;
+        const int64_t gwarp = gthread >> 5;
+        const int64_t nwarps = nthreads >> 5;
         for (int64_t w = gwarp; w < n_items; w += nwarps) {
-            if (w < n_seg) {
+            if (w >= Pd) {
+                const int64_t wl = w - Pd;
                 int F = 0;
-                while (F + 1 < nF && w >= seg_begin[F + 1]) ++F;
-                const int64_t sg = Gr.seg_off[F][b] + (w - seg_begin[F]);
+                while (F + 1 < nF && wl >= long_begin[F + 1]) ++F;
+                const int64_t sg = Gr.seg_off[F][b] + (wl - long_begin[F]);
+                const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
                 const int32_t row = __ldg(Gr.seg_row[F] + sg);
                 const int32_t st = __ldg(Gr.seg_start[F] + sg);
-                const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
                 float sum[JPR];
                 {
                     Kahan k[JPR];
 #pragma unroll
                     for (int j = 0; j < JPR; ++j) k[j].init();
-                    const float* src = A.contrib[F] + (int64_t)st * JPR;
-                    for (int e = lane; e < cnt; e += 32) {
-#pragma unroll
-                        for (int q = 0; q < JPR / 4; ++q) {
-                            const float4 v = ld4_cg(src + (int64_t)e * JPR + 4 * q);
-                            k[4 * q + 0].add(v.x);
-                            k[4 * q + 1].add(v.y);
-                            k[4 * q + 2].add(v.z);
-                            k[4 * q + 3].add(v.w);
-                        }
-                    }
+                    rows_sum<JPR / 4>(A.contrib[F] + (int64_t)st * JPR, JPR, lane, 32, cnt, k);
 #pragma unroll
                     for (int j = 0; j < JPR; ++j) sum[j] = k[j].value();
                 }
-                if (cnt > 1) {
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1)
+                for (int o = 1; o < 32; o <<= 1)
 #pragma unroll
-                        for (int j = 0; j < JPR; ++j) sum[j] += __shfl_xor_sync(0xffffffffu, sum[j], o);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < JPR; ++j) sum[j] = __shfl_sync(0xffffffffu, sum[j], 0);
-                }
+                    for (int j = 0; j < JPR; ++j) sum[j] += __shfl_xor_sync(0xffffffffu, sum[j], o);
                 if (lane < JPR / 4) {
                     const float sc = -eta / (A.row_mean ? (float)cnt : 1.f);
                     float* base = (F < P.N ? P.U[F] : P.V[F - P.N]) + (int64_t)row * JPR + 4 * lane;
@@ -216,10 +320,19 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                     st4(base, u);
                 }
             } else {
-                const int64_t l = w - n_seg;
+                const int64_t l = w;
                 Kahan k;
                 k.init();
-                for (int64_t pi = lane; pi < gridDim.x; pi += 32) k.add(__ldcg(A.core_part + pi * Pd + l));
+                // four partials' loads in flight per lane, added in partial order
+                int64_t pi = lane;
+                for (; pi + 96 < n_part; pi += 128) {
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldcg(A.core_part + (pi + 32 * u) * Pd + l);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) k.add(v[u]);
+                }
+                for (; pi < n_part; pi += 32) k.add(__ldcg(A.core_part + pi * Pd + l));
                 float sum = k.value();
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -243,7 +356,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
 static size_t mb_smem(int N, int JP) {
     size_t q = 1;
     for (int n = 0; n < N - 1; ++n) q *= JP;
-    return sizeof(float) * (q * round4(JP) + (size_t)N * kTile * round4(JP));
+    return sizeof(float) * (q * round4(JP) + (size_t)N * mb_stage_rows(N) * round4(JP));
 }
 
 int minibatch_epoch_grid(int N, int JP, int num_sms) {

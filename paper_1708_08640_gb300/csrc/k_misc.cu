@@ -126,89 +126,137 @@ cudaError_t launch_coupled_fwd(const DParams& P, int m, const int32_t* r, const 
 }
 
 // ------------------------------------------------------------------ segments
-// One warp per segment: the lanes stride over the segment's events (slot order), keep
-// Neumaier-compensated sums, and combine them with a fixed xor butterfly, so every lane
-// ends with the same, run-to-run identical, sum.
+// Every segment's events are summed in slot order with Neumaier compensation.  Short
+// segments (the common case: rows touched a few times in a group) take one thread each;
+// long ones a warp whose lanes stride over the events, huge ones (the hottest rows of a
+// large group) a CTA whose threads stride over them.  Strided partial sums are combined
+// with a fixed xor butterfly and, across warps, in warp order, so every sum is run-to-run
+// identical.
+template <int C4>
+__device__ __forceinline__ void segment_finish(const DParams& P, const SegmentLaunch& S, int F,
+                                               int32_t row, int32_t cnt, const float* sum,
+                                               const float* eta_p, int row_mean, int mode,
+                                               int j_begin, int j_end) {
+    const int ld = 4 * C4;
+    if (mode == 0) {
+        const float sc = -(*eta_p) / (row_mean ? (float)cnt : 1.f);
+        float* base = (F < P.N ? P.U[F] : P.V[F - P.N]) + (int64_t)row * ld;
+        for (int j = j_begin; j < j_end; ++j) base[j] = fmaf(sc, sum[j], base[j]);
+    } else {
+        const int Jf = S.Jf[F];
+        float* o = S.out[F] + (int64_t)row * Jf;
+        float* cmp = S.comp[F] + (int64_t)row * Jf;
+        for (int j = j_begin; j < min(j_end, Jf); ++j) {
+            Kahan k;
+            k.s = o[j];
+            k.c = cmp[j];
+            k.add(sum[j]);
+            o[j] = k.s;
+            cmp[j] = k.c;
+        }
+    }
+}
+
 template <int C4>
 __global__ void __launch_bounds__(256) k_segments(DParams P, DGroup Gr, SegmentLaunch S,
                                                   const float* eta_p, int row_mean, int mode) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= S.total_segs) return;
-    int F = 0;
-    while (F + 1 < S.nF && w >= S.seg_begin[F + 1]) ++F;
-    const int64_t sg = Gr.seg_off[F][S.g] + (w - S.seg_begin[F]);
-    const int32_t row = __ldg(Gr.seg_row[F] + sg);
-    const int32_t st = __ldg(Gr.seg_start[F] + sg);
-    const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
     const int ld = 4 * C4;
-    float sum[4 * C4];
-    {
-        Kahan k[4 * C4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    __shared__ float red[8][4 * C4];
+    // pass 0: a CTA per huge segment
+    for (int64_t w = blockIdx.x; w < S.huge_begin[S.nF]; w += gridDim.x) {
+        int F = 0;
+        while (F + 1 < S.nF && w >= S.huge_begin[F + 1]) ++F;
+        const int64_t sg = Gr.seg_off[F][S.g] + (w - S.huge_begin[F]);
+        const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
+        const int32_t row = __ldg(Gr.seg_row[F] + sg);
+        const float* src = S.contrib[F] + (int64_t)__ldg(Gr.seg_start[F] + sg) * ld;
+        float sum[4 * C4];
+        {
+            Kahan k[4 * C4];
 #pragma unroll
-        for (int j = 0; j < 4 * C4; ++j) k[j].init();
-        const float* src = S.contrib[F] + (int64_t)st * ld;
-        for (int e = lane; e < cnt; e += 32) {
+            for (int j = 0; j < 4 * C4; ++j) k[j].init();
+            rows_sum<C4>(src, ld, threadIdx.x, blockDim.x, cnt, k);
 #pragma unroll
-            for (int q = 0; q < C4; ++q) {
-                const float4 v = ld4_cg(src + (int64_t)e * ld + 4 * q);
-                k[4 * q + 0].add(v.x);
-                k[4 * q + 1].add(v.y);
-                k[4 * q + 2].add(v.z);
-                k[4 * q + 3].add(v.w);
-            }
+            for (int j = 0; j < 4 * C4; ++j) sum[j] = k[j].value();
         }
-#pragma unroll
-        for (int j = 0; j < 4 * C4; ++j) sum[j] = k[j].value();
-    }
-    if (cnt > 1) {
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1)
 #pragma unroll
             for (int j = 0; j < 4 * C4; ++j) sum[j] += __shfl_xor_sync(0xffffffffu, sum[j], o);
-    } else {
+        if (lane == 0)
 #pragma unroll
-        for (int j = 0; j < 4 * C4; ++j) sum[j] = __shfl_sync(0xffffffffu, sum[j], 0);
-    }
-    if (mode == 0) {
-        if (lane < C4) {
-            const float eta = *eta_p;
-            const float sc = -eta / (row_mean ? (float)cnt : 1.f);
-            float* base = (F < P.N ? P.U[F] : P.V[F - P.N]) + (int64_t)row * ld + 4 * lane;
-            float4 u = *reinterpret_cast<float4*>(base);
-            float4 d;
-#pragma unroll
-            for (int q = 0; q < C4; ++q)
-                if (q == lane) d = make_float4(sum[4 * q], sum[4 * q + 1], sum[4 * q + 2], sum[4 * q + 3]);
-            u.x = fmaf(sc, d.x, u.x);
-            u.y = fmaf(sc, d.y, u.y);
-            u.z = fmaf(sc, d.z, u.z);
-            u.w = fmaf(sc, d.w, u.w);
-            *reinterpret_cast<float4*>(base) = u;
-        }
-    } else {
-        const int Jf = S.Jf[F];
-        if (lane < Jf) {
-            float v = 0.f;
-#pragma unroll
-            for (int j = 0; j < 4 * C4; ++j)
-                if (j == lane) v = sum[j];
-            float* o = S.out[F] + (int64_t)row * Jf + lane;
-            float* cmp = S.comp[F] + (int64_t)row * Jf + lane;
+            for (int j = 0; j < 4 * C4; ++j) red[warp][j] = sum[j];
+        __syncthreads();
+        if (threadIdx.x < ld) {
+            const int j = threadIdx.x;
             Kahan k;
-            k.s = *o;
-            k.c = *cmp;
-            k.add(v);
-            *o = k.s;
-            *cmp = k.c;
+            k.init();
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) k.add(red[i][j]);
+            float one[4 * C4];
+#pragma unroll
+            for (int i = 0; i < 4 * C4; ++i) one[i] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4 * C4; ++i)
+                if (i == j) one[i] = k.value();
+            segment_finish<C4>(P, S, F, row, cnt, one, eta_p, row_mean, mode, j, j + 1);
         }
+        __syncthreads();
+    }
+    // pass 1: a thread per short segment
+    for (int64_t w = gthread; w < S.short_begin[S.nF]; w += nthreads) {
+        int F = 0;
+        while (F + 1 < S.nF && w >= S.short_begin[F + 1]) ++F;
+        const int64_t sg = Gr.seg_off[F][S.g] + S.nlong[F] + (w - S.short_begin[F]);
+        const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
+        const int32_t row = __ldg(Gr.seg_row[F] + sg);
+        const float* src = S.contrib[F] + (int64_t)__ldg(Gr.seg_start[F] + sg) * ld;
+        float sum[4 * C4];
+        Kahan k[4 * C4];
+#pragma unroll
+        for (int j = 0; j < 4 * C4; ++j) k[j].init();
+        rows_sum<C4>(src, ld, 0, 1, cnt, k);
+#pragma unroll
+        for (int j = 0; j < 4 * C4; ++j) sum[j] = k[j].value();
+        segment_finish<C4>(P, S, F, row, cnt, sum, eta_p, row_mean, mode, 0, ld);
+    }
+    // pass 2: a warp per long (not huge) segment
+    const int64_t gwarp = gthread >> 5, nwarps = nthreads >> 5;
+    for (int64_t w = gwarp; w < S.long_begin[S.nF]; w += nwarps) {
+        int F = 0;
+        while (F + 1 < S.nF && w >= S.long_begin[F + 1]) ++F;
+        const int64_t sg = Gr.seg_off[F][S.g] + S.nhuge[F] + (w - S.long_begin[F]);
+        const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
+        const int32_t row = __ldg(Gr.seg_row[F] + sg);
+        const float* src = S.contrib[F] + (int64_t)__ldg(Gr.seg_start[F] + sg) * ld;
+        float sum[4 * C4];
+        {
+            Kahan k[4 * C4];
+#pragma unroll
+            for (int j = 0; j < 4 * C4; ++j) k[j].init();
+            rows_sum<C4>(src, ld, lane, 32, cnt, k);
+#pragma unroll
+            for (int j = 0; j < 4 * C4; ++j) sum[j] = k[j].value();
+        }
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1)
+#pragma unroll
+            for (int j = 0; j < 4 * C4; ++j) sum[j] += __shfl_xor_sync(0xffffffffu, sum[j], o);
+        // each lane finishes one or two components
+        const int per = (ld + 31) / 32;
+        segment_finish<C4>(P, S, F, row, cnt, sum, eta_p, row_mean, mode, lane * per,
+                           min(ld, (lane + 1) * per));
     }
 }
 
 cudaError_t launch_segments(const DParams& P, const DGroup& G, const SegmentLaunch& S,
                             const float* eta, int row_mean, int mode, cudaStream_t s) {
-    if (S.total_segs <= 0) return cudaSuccess;
-    const unsigned grid = (unsigned)((S.total_segs * 32 + 255) / 256);
+    const int64_t work = std::max({S.short_begin[S.nF], 32 * S.long_begin[S.nF],
+                                   256 * S.huge_begin[S.nF]});
+    if (work <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
     S3_DISPATCH_C4(P.ld / 4, (k_segments<C4><<<grid, 256, 0, s>>>(P, G, S, eta, row_mean, mode)));
     return cudaGetLastError();
 }
@@ -230,7 +278,16 @@ __global__ void __launch_bounds__(256) k_core(DParams P, int N, int JP, int4 Jv,
     for (int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; l < Pd; l += nwarps) {
         Kahan k;
         k.init();
-        for (int64_t p = lane; p < nparts; p += 32) k.add(__ldcg(parts + p * Pd + l));
+        // four partials' loads in flight per lane, added in partial order
+        int64_t p = lane;
+        for (; p + 96 < nparts; p += 128) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = __ldcg(parts + (p + 32 * u) * Pd + l);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) k.add(v[u]);
+        }
+        for (; p < nparts; p += 32) k.add(__ldcg(parts + p * Pd + l));
         float sum = k.value();
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -517,6 +574,7 @@ __global__ void k_gather(float* dst, const float* src, const int64_t* idx, int64
 cudaError_t launch_gather_f32(float* dst, const float* src, const int64_t* idx, int64_t n,
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    if (!dst || !src || !idx) return cudaErrorInvalidValue;
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
     k_gather<<<grid, 256, 0, s>>>(dst, src, idx, n);
     return cudaGetLastError();

@@ -1,27 +1,28 @@
-// BF16 tensor-core form of the S3CMTF tensor pass (3-way, padded rank JP = 16), sm_103a.
+// BF16 tensor-core form of the S3CMTF tensor pass (3-way, padded rank JP = 16 or 32), sm_103a.
 //
-// For a tile of 256 tensor entries (two halves of 128 = the MMA's M) the three dense
-// contractions of the per-entry work run on the 5th-generation tensor cores (tcgen05.mma,
-// BF16 operands in shared memory, FP32 accumulators in tensor memory):
-//   stage 1   T  = A3 . G_(3)^T      [128 entries x JP^2 pairs]  (Def. 4, Alg. 3: the core
+// A CTA of 128 threads takes tiles of 128 tensor entries (the MMA's M), one entry per
+// thread and TMEM lane.  The three dense contractions of the per-entry work run on the
+// 5th-generation tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32
+// accumulators in tensor memory), chunk by chunk of 128 (j1, j2) pairs:
+//   stage 1   T  = A3 . G_(3)^T      [128 entries x 128 pairs]   (Def. 4, Alg. 3: the core
 //                                      contracted with the last mode's rows)
-//   partial   P3 = KR . G_(3)        [128 entries x JP]          (p_3 = G x_{-3} {a})
-//   core      dG = KR^T . (e o A3)   [JP^2 pairs x JP]           (sum_b e_b a1 o a2 o a3)
+//   partial   P3 = KR . G_(3)        [128 entries x JP]           (p_3 = G x_{-3} {a})
+//   core      dG = KR^T . (e o A3)   [128 pairs x JP]             (sum_b e_b a1 o a2 o a3)
 // with KR[b] = a1_b (x) a2_b (the Khatri-Rao row of the entry).  The rest runs on CUDA cores
 // in FP32: p_1 = T a_2, p_2 = T^T a_1 and x~ = a_1 . p_1 from each thread's TMEM lane, the
 // error e = x - x~, the row gradients of Eq. (8) and the row / core steps.  FP32 master
 // parameters; BF16 only for the tensor-core operands.
 //
 // Shared-memory operands (no swizzle, 8 x 16-byte core matrices; see tc.cuh):
-//   sG   the core once, element (j3, pair) at (pair/8)*(JP/8)*128 + (j3/8)*128
-//        + (j3%8)*16 + (pair%8)*2: MN-major B of stage 1 (K = j3, N = pair) and K-major B of
-//        the partial (K = pair, N = j3), both read from the same bytes
-//   sA3  per half, K-major A (M = entry, K = j3)
-//   sKR  per half and 128-pair chunk, K-major A of the partial (M = entry, K = pair) and,
-//        read as MN-major, the A operand of the core GEMM (M = pair, K = entry)
-//   sEA3 e*a3 of all 256 entries, MN-major B of the core GEMM (K = entry, N = j3)
-// TMEM (512 columns): T of both halves [0, 256), P3 of both halves [256, 256 + 2 JP),
-// dG per chunk [256 + 2 JP, 256 + 2 JP + NC JP).
+//   sG   the core, element (j3, pair) at (pair/8)*(JP/8)*128 + (j3/8)*128 + (j3%8)*16
+//        + (pair%8)*2: MN-major B of stage 1 (K = j3, N = pair) and K-major B of the
+//        partial (K = pair, N = j3), both read from the same bytes
+//   sA3  K-major A of stage 1 (M = entry, K = j3)
+//   sKR  one 128-pair chunk, K-major A of the partial (M = entry, K = pair) and, read as
+//        MN-major, the A operand of the core GEMM (M = pair, K = entry)
+//   sEA3 e*a3, MN-major B of the core GEMM (K = entry, N = j3)
+// TMEM (256 columns, so that two CTAs share an SM): T of one chunk [0, 128), P3
+// [128, 128 + JP), dG of one chunk [128 + JP, 128 + 2 JP).
 #include <cuda_runtime.h>
 
 #include "hog_common.cuh"
@@ -30,28 +31,33 @@
 
 namespace s3 {
 
-constexpr int kBfTile = 256;    // entries per tile (two MMA halves)
+constexpr int kBfTile = 128;    // entries per tile (the MMA's M)
 constexpr int kChunk = 128;     // pairs per chunk (the N of stage 1, the M of the core GEMM)
 constexpr int kWaitLimit = 1 << 24;
+constexpr uint32_t kTmemCols = 256;
+// more than a third of an SM's shared memory, so that no more than two CTAs (2 x 256 TMEM
+// columns) are ever resident on one SM
+constexpr size_t kBfMinSmem = 80 * 1024;
 
 template <int JP>
 struct BfLayout {
-    static_assert(JP == 16, "the BF16 form is built for padded rank 16");
+    static_assert(JP == 16 || JP == 32, "the BF16 form is built for padded ranks 16 and 32");
     static constexpr int NPAIR = JP * JP;
     static constexpr int NC = NPAIR / kChunk;
     static constexpr uint32_t G_BYTES = JP * NPAIR * 2;
-    static constexpr uint32_t A3_BYTES = 128 * JP * 2;           // per half
-    static constexpr uint32_t KR_BYTES = 128 * kChunk * 2;       // per half
+    static constexpr uint32_t A3_BYTES = kBfTile * JP * 2;
+    static constexpr uint32_t KR_BYTES = kBfTile * kChunk * 2;
     static constexpr uint32_t EA3_BYTES = kBfTile * JP * 2;
     static constexpr uint32_t OFF_G = 0;
     static constexpr uint32_t OFF_A3 = OFF_G + G_BYTES;
-    static constexpr uint32_t OFF_KR = OFF_A3 + 2 * A3_BYTES;
-    static constexpr uint32_t OFF_EA3 = OFF_KR + 2 * KR_BYTES;
-    static constexpr uint32_t OFF_ACC = OFF_EA3 + EA3_BYTES;     // row accumulators (floats)
+    static constexpr uint32_t OFF_KR = OFF_A3 + A3_BYTES;
+    static constexpr uint32_t OFF_EA3 = OFF_KR + KR_BYTES;
+    static constexpr uint32_t OFF_SLOTS = OFF_EA3 + EA3_BYTES;   // row gradient slots (floats)
     static constexpr uint32_t COL_T = 0;
-    static constexpr uint32_t COL_P3 = 256;
-    static constexpr uint32_t COL_DG = 256 + 2 * JP;
-    static_assert(COL_DG + NC * JP <= 512, "TMEM budget");
+    static constexpr uint32_t COL_P3 = kChunk;
+    static constexpr uint32_t COL_DG = kChunk + JP;
+    static_assert(COL_DG + JP <= kTmemCols, "TMEM budget");
+    static_assert(OFF_SLOTS % 16 == 0, "slot rows are written with 16-byte stores");
 };
 
 // one 16-byte chunk of 8 BF16 values
@@ -61,8 +67,14 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  "r"(d) : "memory");
 }
 
+// byte offset of core element (j3, pair) in sG
 template <int JP>
-__global__ void __launch_bounds__(kBfTile, 1)
+__device__ __forceinline__ uint32_t g_off(int pair, int j3) {
+    return (uint32_t)((pair / 8) * (JP / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16 + (pair % 8) * 2);
+}
+
+template <int JP>
+__global__ void __launch_bounds__(kBfTile, 2)
 k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, const float* eta_p,
                   int row_mean, float core_step_scale, HogSmem H, int* err_flag) {
     using Lt = BfLayout<JP>;
@@ -74,16 +86,15 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ int s_tile;
     __shared__ int s_fail;   // set when a bounded wait ran out; read after barriers only
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int half = tid >> 7, r = tid & 127;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = smem_u32(smem_raw);
     const uint32_t sG = sbase + Lt::OFF_G;
-    const uint32_t sA3 = sbase + Lt::OFF_A3 + half * Lt::A3_BYTES;
-    const uint32_t sKR0 = sbase + Lt::OFF_KR;
-    const uint32_t sKR = sKR0 + half * Lt::KR_BYTES;
+    const uint32_t sA3 = sbase + Lt::OFF_A3;
+    const uint32_t sKR = sbase + Lt::OFF_KR;
     const uint32_t sEA3 = sbase + Lt::OFF_EA3;
+    const __nv_bfloat16* gbf = reinterpret_cast<const __nv_bfloat16*>(smem_raw + Lt::OFF_G);
     const float eta = *eta_p;
-    if (warp == 0) tmem_alloc(&s_tmem, 512);
+    if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
     if (tid == 0) {
         mbar_init(&s_mbar, 1);
         s_fail = 0;
@@ -92,25 +103,29 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
     uint32_t phase = 0;
 
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+    __syncthreads();
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
-        __syncthreads();
         const int64_t t = s_tile;
         if (t >= n_tiles || s_fail) break;
-        // ---- the current core as BF16 operand (two 16-byte chunks of 8 pairs per thread)
-        for (int ch = tid; ch < JP * Lt::NPAIR / 8; ch += kBfTile) {
-            const int pg = ch / JP, j3 = ch % JP;      // 8 pairs starting at 8 pg, one j3
-            float v[8];
+        // the next tile is claimed now; its index is needed only at the end of this one
+        int next = 0;
+        if (tid == 0) next = atomicAdd(tile_counter, 1);
+        hog_tables(Gr, t, smem, H, tid, kBfTile);
+        // ---- the current core as BF16 operand: coalesced float4 reads of G (pair-major),
+        //      each element stored at its place in the (j3, pair) core-matrix layout
+        for (int l = tid * 4; l < Lt::NPAIR * JP; l += kBfTile * 4) {
+            const float4 v = ld4_cg(P.G + l);
+            const int pair = l / JP, j0 = l % JP;
+            const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = __ldcg(P.G + (int64_t)(8 * pg + i) * JPR + j3);
-            const uint32_t off = pg * (JP / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16;
-            st_shared_v4(sG + off, pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                         pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+            for (int i = 0; i < 4; ++i)
+                *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j0 + i)) =
+                    __float2bfloat16_rn(vv[i]);
         }
-        hog_clear<JPR>(smem, Gr, t, H);
         // ---- this thread's entry
         const int64_t e0 = Gr.t_off[t];
         const int nb = (int)(Gr.t_off[t + 1] - e0);
@@ -134,7 +149,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         // A3 row (K-major, M = entry)
 #pragma unroll
         for (int kg = 0; kg < JP / 8; ++kg) {
-            const uint32_t off = (r / 8) * (JP / 8) * 128 + kg * 128 + (r % 8) * 16;
+            const uint32_t off = (tid / 8) * (JP / 8) * 128 + kg * 128 + (tid % 8) * 16;
             st_shared_v4(sA3 + off, pack_bf16x2(a3[8 * kg], a3[8 * kg + 1]),
                          pack_bf16x2(a3[8 * kg + 2], a3[8 * kg + 3]),
                          pack_bf16x2(a3[8 * kg + 4], a3[8 * kg + 5]),
@@ -153,15 +168,12 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 tc_fence_after();
                 constexpr uint32_t idesc = tc_idesc_bf16(128, kChunk, 0, 1);
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int ks = 0; ks < JP / 16; ++ks) {
-                        const uint64_t ad = tc_sdesc(sbase + Lt::OFF_A3 + h * Lt::A3_BYTES + ks * 256,
-                                                     128, (JP / 8) * 128);
-                        const uint64_t bd = tc_sdesc(sG + (kChunk / 8) * c * (JP / 8) * 128 + ks * 256,
-                                                     128, (JP / 8) * 128);
-                        tc_mma(tmem + Lt::COL_T + h * kChunk, ad, bd, idesc, ks > 0);
-                    }
+                for (int ks = 0; ks < JP / 16; ++ks) {
+                    const uint64_t ad = tc_sdesc(sA3 + ks * 256, 128, (JP / 8) * 128);
+                    const uint64_t bd = tc_sdesc(sG + (kChunk / 8) * c * (JP / 8) * 128 + ks * 256,
+                                                 128, (JP / 8) * 128);
+                    tc_mma(tmem + Lt::COL_T, ad, bd, idesc, ks > 0);
+                }
                 tc_commit(&s_mbar);
             }
             if (!mbar_wait(&s_mbar, phase, kWaitLimit)) s_fail = 1;
@@ -170,7 +182,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
 #pragma unroll
             for (int q = 0; q < kChunk / 32; ++q) {
                 float v[32];
-                tmem_ld32(lane_base + Lt::COL_T + half * kChunk + 32 * q, v);
+                tmem_ld32(lane_base + Lt::COL_T + 32 * q, v);
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int pair = kChunk * c + 32 * q + i;
@@ -179,6 +191,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     p2[j2] = fmaf(v[i], a1[j1], p2[j2]);
                 }
             }
+            // every lane has read T before the next chunk's MMA overwrites it
             tc_fence_before();
             __syncthreads();
         }
@@ -195,7 +208,11 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                          pack_bf16x2(err * a3[8 * jg + 4], err * a3[8 * jg + 5]),
                          pack_bf16x2(err * a3[8 * jg + 6], err * a3[8 * jg + 7]));
         }
-        // ---- partial p3 and core gradient, chunk by chunk of Khatri-Rao rows
+        // ---- partial p3 and core gradient, chunk by chunk of Khatri-Rao rows; each chunk's
+        //      share of the core step leaves as soon as its dG is in TMEM:
+        //      G += eta cs / W (dG / n_t - lambda_reg / |Omega| G)   (lock-free)
+        const float sc = nb > 0 ? eta * core_step_scale / (float)nb : 0.f;
+        const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
 #pragma unroll
@@ -206,7 +223,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     const int pair = kChunk * c + 8 * kg + i;
                     w[i] = a1[pair / JP] * a2[pair % JP];
                 }
-                const uint32_t off = (r / 8) * (kChunk / 8) * 128 + kg * 128 + (r % 8) * 16;
+                const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
                 st_shared_v4(sKR + off, pack_bf16x2(w[0], w[1]), pack_bf16x2(w[2], w[3]),
                              pack_bf16x2(w[4], w[5]), pack_bf16x2(w[6], w[7]));
             }
@@ -215,114 +232,176 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                // P3[h] += KR[h] . G_(3)[chunk]   (M = 128 entries, N = JP, K = 128 pairs)
+                // P3 += KR . G_(3)[chunk]   (M = 128 entries, N = JP, K = 128 pairs)
                 constexpr uint32_t id_p3 = tc_idesc_bf16(128, JP, 0, 0);
 #pragma unroll
-                for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int ks = 0; ks < kChunk / 16; ++ks) {
-                        const uint64_t ad = tc_sdesc(sKR0 + h * Lt::KR_BYTES + ks * 256, 128,
-                                                     (kChunk / 8) * 128);
-                        const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JP / 8) * 128,
-                                                     (JP / 8) * 128, 128);
-                        tc_mma(tmem + Lt::COL_P3 + h * JP, ad, bd, id_p3, (c > 0 || ks > 0));
-                    }
-                // dG[c] = KR^T . (e o A3)   (M = 128 pairs, N = JP, K = 256 entries)
+                for (int ks = 0; ks < kChunk / 16; ++ks) {
+                    const uint64_t ad = tc_sdesc(sKR + ks * 256, 128, (kChunk / 8) * 128);
+                    const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JP / 8) * 128,
+                                                 (JP / 8) * 128, 128);
+                    tc_mma(tmem + Lt::COL_P3, ad, bd, id_p3, (c > 0 || ks > 0));
+                }
+                // dG[chunk] = KR^T . (e o A3)   (M = 128 pairs, N = JP, K = 128 entries)
                 constexpr uint32_t id_dg = tc_idesc_bf16(128, JP, 1, 1);
 #pragma unroll
                 for (int ks = 0; ks < kBfTile / 16; ++ks) {
-                    const int h = ks / 8, kk = ks % 8;
-                    const uint64_t ad = tc_sdesc(sKR0 + h * Lt::KR_BYTES + kk * 2 * (kChunk / 8) * 128,
-                                                 (kChunk / 8) * 128, 128);
+                    const uint64_t ad = tc_sdesc(sKR + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
                     const uint64_t bd = tc_sdesc(sEA3 + ks * 256, 128, (kBfTile / 8) * 128);
-                    tc_mma(tmem + Lt::COL_DG + c * JP, ad, bd, id_dg, ks > 0);
+                    tc_mma(tmem + Lt::COL_DG, ad, bd, id_dg, ks > 0);
                 }
                 tc_commit(&s_mbar);
             }
             if (!mbar_wait(&s_mbar, phase, kWaitLimit)) s_fail = 1;
             phase ^= 1;
             tc_fence_after();
+            if (nb > 0) {
+                // lane tid holds pair kChunk*c + tid; the regulariser reads the BF16 copy of
+                // G (its term, eta cs lambda / (W |Omega|) G, sits far below G's FP32 ulp)
+                const int pair = kChunk * c + tid;
+                float* g = P.G + (int64_t)pair * JPR;
+#pragma unroll
+                for (int h = 0; h < JP / 16; ++h) {
+                    float d[16];
+                    tmem_ld16(lane_base + Lt::COL_DG + 16 * h, d);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        float gv[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+                            gv[i] = __bfloat162float(gbf[g_off<JP>(pair, 16 * h + 4 * q + i) / 2]);
+                        red_add_v4(g + 16 * h + 4 * q, fmaf(sc, d[4 * q], -rg * gv[0]),
+                                   fmaf(sc, d[4 * q + 1], -rg * gv[1]),
+                                   fmaf(sc, d[4 * q + 2], -rg * gv[2]),
+                                   fmaf(sc, d[4 * q + 3], -rg * gv[3]));
+                    }
+                }
+            }
+            // every lane has read dG, and the MMAs have read KR, before the next chunk
+            tc_fence_before();
+            __syncthreads();
         }
-        // ---- row gradients (Eq. (8)) into the tile's accumulators
+        // ---- row gradients (Eq. (8)) into the tile's slots
         {
             float p3[JP];
-            tmem_ld16(lane_base + Lt::COL_P3 + half * JP, p3);
+#pragma unroll
+            for (int h = 0; h < JP / 16; ++h) {
+                float v[16];
+                tmem_ld16(lane_base + Lt::COL_P3 + 16 * h, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) p3[16 * h + i] = v[i];
+            }
             if (valid) {
                 const float r0 = P.lambda_reg * __ldg(P.inv_cnt[0] + row[0]);
                 const float r1 = P.lambda_reg * __ldg(P.inv_cnt[1] + row[1]);
                 const float r2 = P.lambda_reg * __ldg(P.inv_cnt[2] + row[2]);
-                float* s0 = smem + H.off[0] + __ldg(Gr.tpos[0] + e) * JPR;
-                float* s1 = smem + H.off[1] + __ldg(Gr.tpos[1] + e) * JPR;
-                float* s2 = smem + H.off[2] + __ldg(Gr.tpos[2] + e) * JPR;
+                float c[JPR];
 #pragma unroll
-                for (int j = 0; j < JP; ++j) {
-                    atomicAdd(s0 + j, fmaf(-err, p1[j], r0 * a1[j]));
-                    atomicAdd(s1 + j, fmaf(-err, p2[j], r1 * a2[j]));
-                    atomicAdd(s2 + j, fmaf(-err, p3[j], r2 * a3[j]));
-                }
+                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p1[j], r0 * a1[j]);
+                put_slot<JPR>(smem, H, 0, __ldg(Gr.tpos[0] + e), c);
+#pragma unroll
+                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p2[j], r1 * a2[j]);
+                put_slot<JPR>(smem, H, 1, __ldg(Gr.tpos[1] + e), c);
+#pragma unroll
+                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
+                put_slot<JPR>(smem, H, 2, __ldg(Gr.tpos[2] + e), c);
             }
         }
-        // ---- this tile's share of the core step, lock-free:
-        //      G += eta cs / W (dG / n_t - lambda_reg / |Omega| G)
-        if (nb > 0) {
-            const float sc = eta * core_step_scale / (float)nb;
-            const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
-            for (int c = half; c < NC; c += 2) {
-                float d[JP];
-                tmem_ld16(lane_base + Lt::COL_DG + c * JP, d);
-                const int pair = kChunk * c + r;
-                float* g = P.G + (int64_t)pair * JPR;
-#pragma unroll
-                for (int q = 0; q < JP / 4; ++q) {
-                    const float4 gv = ld4_cg(g + 4 * q);
-                    red_add_v4(g + 4 * q, fmaf(sc, d[4 * q], -rg * gv.x),
-                               fmaf(sc, d[4 * q + 1], -rg * gv.y),
-                               fmaf(sc, d[4 * q + 2], -rg * gv.z),
-                               fmaf(sc, d[4 * q + 3], -rg * gv.w));
-                }
-            }
-        }
-        hog_coupled<JP>(P, Gr, t, smem, H);
+        hog_coupled<JP>(P, Gr, t, smem, H, tid, kBfTile);
         tc_fence_before();
         __syncthreads();
-        hog_flush<JPR>(P, Gr, t, smem, H, eta, row_mean);
+        hog_flush<JPR>(P, smem, H, eta, row_mean);
+        if (tid == 0) s_tile = next;
         __syncthreads();
     }
     tc_fence_before();
     __syncthreads();
     if (s_fail && tid == 0) atomicExch(err_flag, 1);
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
-size_t tensor_hog_bf16_smem(int JP, const int64_t* max_segs, int nF) {
-    if (JP != 16) return 0;
-    size_t b = BfLayout<16>::OFF_ACC;
-    for (int F = 0; F < nF; ++F) b += (size_t)max_segs[F] * JP * sizeof(float);
-    return b;
+static size_t bf16_fixed_bytes(int JP) {
+    return JP == 16 ? BfLayout<16>::OFF_SLOTS : JP == 32 ? BfLayout<32>::OFF_SLOTS : 0;
+}
+
+size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF) {
+    const size_t fixed = bf16_fixed_bytes(JP);
+    if (!fixed) return 0;
+    const size_t b = hog_smem_floats(JP, max_events, max_segs, nF, nullptr, fixed / sizeof(float)) *
+                     sizeof(float);
+    return b < kBfMinSmem ? kBfMinSmem : b;
+}
+
+int tensor_hog_bf16_tile() { return kBfTile; }
+
+// the dynamic shared-memory limit, and the largest shared-memory carveout: two CTAs of this
+// kernel need most of an SM's shared memory
+template <typename K>
+static cudaError_t prep_bf16(K kernel, size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
+template <int JP>
+static cudaError_t launch_bf16(const DParams& P, const DGroup& G, int64_t n_tiles, int* tile_counter,
+                               int grid, const float* eta, int row_mean, float core_step_scale,
+                               const HogSmem& H, size_t smem, int* err_flag, cudaStream_t s) {
+    cudaError_t e = prep_bf16(k_tensor_hog_bf16<JP>, smem);
+    if (e != cudaSuccess) return e;
+    k_tensor_hog_bf16<JP><<<grid, kBfTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
+                                                      core_step_scale, H, err_flag);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
-                                   float core_step_scale, const int64_t* max_segs, int* err_flag,
-                                   cudaStream_t s) {
-    if (JP != 16 || P.N != 3) return cudaErrorInvalidValue;
+                                   float core_step_scale, const int64_t* max_events,
+                                   const int64_t* max_segs, int* err_flag, cudaStream_t s) {
+    const size_t fixed = bf16_fixed_bytes(JP);
+    if (!fixed || P.N != 3) return cudaErrorInvalidValue;
     if (n_tiles <= 0) return cudaSuccess;
-    HogSmem H;
-    H.nF = P.N + P.M;
-    // accumulator offsets in floats from the start of dynamic shared memory
-    size_t off = BfLayout<16>::OFF_ACC / sizeof(float);
-    for (int F = 0; F < H.nF; ++F) {
-        H.off[F] = (int)off;
-        off += (size_t)max_segs[F] * JP;
+    HogSmem H{};
+    size_t smem = hog_smem_floats(JP, max_events, max_segs, P.N + P.M, &H, fixed / sizeof(float)) *
+                  sizeof(float);
+    if (smem < kBfMinSmem) smem = kBfMinSmem;
+    if (JP == 16)
+        return launch_bf16<16>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
+                               smem, err_flag, s);
+    return launch_bf16<32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
+                           smem, err_flag, s);
+}
+
+// CTAs of the BF16 kernel that fit on one SM with this much dynamic shared memory (at most
+// two: two CTAs take all 512 TMEM columns), from the device's shared-memory and register
+// limits and the kernel's static resources.  (A CTA launched beyond what fits only runs once
+// another has finished: the kernel has no inter-CTA waits, so it would find no tile left.)
+int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaErrorInvalidValue;
+    if (JP == 16) {
+        e = prep_bf16(k_tensor_hog_bf16<16>, smem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<16>);
+    } else if (JP == 32) {
+        e = prep_bf16(k_tensor_hog_bf16<32>, smem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<32>);
     }
-    const size_t smem = off * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_tensor_hog_bf16<16>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_tensor_hog_bf16<16><<<grid, kBfTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
-                                                      core_step_scale, H, err_flag);
-    return cudaGetLastError();
+    if (e != cudaSuccess) return 0;
+    int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm_regs, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess)
+        return 0;
+    const size_t per_cta = smem + fa.sharedSizeBytes + (size_t)reserved;
+    const int by_smem = (int)((size_t)sm_smem / per_cta);
+    // registers are allocated per warp in units of 256
+    const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = sm_regs / (warp_regs * (kBfTile / 32));
+    int nb = by_smem < by_regs ? by_smem : by_regs;
+    return nb < 2 ? nb : 2;
 }
 
 }  // namespace s3

@@ -16,28 +16,39 @@ struct TensorLaunch {
 
 // Shared-memory bytes of the FP32 tensor kernels (for cudaFuncSetAttribute / launch).
 size_t tensor_contrib_smem(int N, int JP);
-size_t tensor_hog_smem(int N, int JP, const int64_t* max_segs_per_factor, int n_factors);
+size_t tensor_hog_smem(int N, int JP, int L, const int64_t* max_events, const int64_t* max_segs,
+                       int64_t ccap, int n_factors);
 
-// Minibatch / gradient: contributions of every tensor entry in [e_begin, e_end) written
-// to their slots, and the CTA partials of sum e a1 o..o aN.  One CTA per kTile entries.
+// Gradient: contributions of every tensor entry in [e_begin, e_end) written to their slots,
+// and one partial of sum e a1 o..o aN per CTA (at most max_grid CTAs, grid-stride over
+// tiles); *grid_out = the number of partials written.
 cudaError_t launch_tensor_contrib(int N, int JP, const DParams& P, const DGroup& G,
-                                  const TensorLaunch& L, cudaStream_t s);
+                                  const TensorLaunch& L, int max_grid, int* grid_out,
+                                  cudaStream_t s);
 
 // HOGWILD epoch: n_tiles tiles claimed from *tile_counter (zeroed by the caller) by `grid`
-// persistent CTAs; rows updated atomically with step -eta * damp * (sum or mean per tile);
+// persistent CTAs; rows updated atomically with step -eta * (the row's step scale,
+// row_damp) * (sum or mean per tile);
 // each tile adds core_step_scale * eta * (its mean core step) to G atomically.
-// max_segs[F]: the largest number of segments of factor F in any tile (sizes the row
-// accumulators in shared memory; see tensor_hog_smem).
-cudaError_t launch_tensor_hog(int N, int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
-                              int* tile_counter, int grid, const float* eta, int row_mean,
-                              float core_step_scale, const int64_t* max_segs, cudaStream_t s);
+// The grouping numbers events by slot (POS_SLOT); max_events[F]: the largest number of events
+// of factor F in any tile (sizes the gradient slots in shared memory; see tensor_hog_smem).
+// L: lanes per entry (tensor_hog_lanes).
+// ccap: the most coupled entries (all matrices) of any tile.
+cudaError_t launch_tensor_hog(int N, int JP, int L, const DParams& P, const DGroup& G,
+                              int64_t n_tiles, int* tile_counter, int grid, const float* eta,
+                              int row_mean, float core_step_scale, const int64_t* max_events,
+                              const int64_t* max_segs, int64_t ccap, cudaStream_t s);
 
-// BF16 tensor-core HOGWILD epoch (N = 3, JP = 16): as launch_tensor_hog, one CTA per SM;
+// BF16 tensor-core HOGWILD epoch (N = 3, JP = 16 or 32): as launch_tensor_hog with tiles of
+// tensor_hog_bf16_tile() entries, at most two CTAs per SM (tensor_hog_bf16_blocks_per_sm);
 // sets *err_flag when a bounded wait on the tensor cores ran out.
-size_t tensor_hog_bf16_smem(int JP, const int64_t* max_segs, int nF);
+int tensor_hog_bf16_tile();
+int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem);
+size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF);
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
-                                   float core_step_scale, const int64_t* max_segs, int* err_flag,
+                                   float core_step_scale, const int64_t* max_events,
+                                   const int64_t* max_segs, int* err_flag,
                                    cudaStream_t s);
 
 // Deterministic minibatch epoch as one cooperative launch of `grid` CTAs (see k_minibatch.cu).
@@ -64,8 +75,11 @@ cudaError_t launch_tensor_fwd(int N, int JP, const DParams& P, const int32_t* co
                               cudaStream_t s);
 
 int tensor_supported_jp(int N, int J);   // smallest instantiated JP >= J, or 0
-// sets the dynamic shared-memory limits of this shape's kernels (before any graph capture)
-cudaError_t tensor_prepare(int N, int JP, size_t hog_smem);
+// lanes per entry of the FP32 HOGWILD kernel for tiles of `tile` entries (tiles hold at
+// most kTile / lanes entries)
+int tensor_hog_lanes(int N, int JP, int64_t tile);
+// sets the dynamic shared-memory limits of this shape's gradient and forward kernels
+cudaError_t tensor_prepare(int N, int JP);
 int tensor_fwd_blocks(int64_t n);        // CTAs (and partial pairs) of launch_tensor_fwd
 
 // Coupled-matrix entries of group range [c_begin, c_end) of matrix m: contributions to
@@ -90,8 +104,14 @@ struct SegmentLaunch {
     float* out[kMaxF];
     float* comp[kMaxF];
     int Jf[kMaxF];
-    int64_t total_segs;     // number of segments of group g over all factors
-    int64_t seg_begin[kMaxF + 1];  // prefix of per-factor segment counts within group g
+    // group g's segments of each factor: the first nhuge[F] have more than kHugeSeg events,
+    // the first nlong[F] (huge included) more than kShortSeg, the rest are short; prefixes
+    // over the factors of the three class sizes
+    int64_t nhuge[kMaxF];
+    int64_t nlong[kMaxF];
+    int64_t huge_begin[kMaxF + 1];
+    int64_t long_begin[kMaxF + 1];    // long, not huge
+    int64_t short_begin[kMaxF + 1];
 };
 cudaError_t launch_segments(const DParams& P, const DGroup& G, const SegmentLaunch& S,
                             const float* eta, int row_mean, int mode, cudaStream_t s);
@@ -136,6 +156,33 @@ cudaError_t launch_core_reg(float* out, const float* G, int N, const int* J, int
 cudaError_t launch_gather_f32(float* dst, const float* src, const int64_t* idx, int64_t n,
                               cudaStream_t s);
 // resident CTAs per SM of the HOGWILD kernel with `smem` dynamic shared memory
-int tensor_hog_blocks_per_sm(int N, int JP, size_t smem);
+int tensor_hog_blocks_per_sm(int N, int JP, int L, size_t smem);
+// the per-variant halves of launch_tensor_hog / tensor_hog_blocks_per_sm (k_tensor_hog2.cu:
+// L = 2; k_tensor_hog4.cu: L = 4 and the 4-way L = 1)
+cudaError_t launch_tensor_hog_l2(int N, int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
+                                 int* tile_counter, int grid, const float* eta, int row_mean,
+                                 float core_step_scale, const int64_t* max_events,
+                                 const int64_t* max_segs, int64_t ccap, cudaStream_t s);
+int tensor_hog_blocks_l2(int N, int JP, size_t smem);
+cudaError_t launch_tensor_hog_l41(int N, int JP, int L, const DParams& P, const DGroup& G,
+                                  int64_t n_tiles, int* tile_counter, int grid, const float* eta,
+                                  int row_mean, float core_step_scale, const int64_t* max_events,
+                                  const int64_t* max_segs, int64_t ccap, cudaStream_t s);
+int tensor_hog_blocks_l41(int N, int JP, int L, size_t smem);
+
+// Final QR step (k_qr.cu).  launch_qr_factor: CholeskyQR2 of U (rows x J of a row-major
+// matrix with leading dimension ld, J <= 32) into R, Rinv (J x J FP64, upper triangular),
+// with scratch parts ([grid][J * J] FP64), R1 and R1inv (J x J); *bad = 1 if U is
+// numerically rank deficient.  launch_qr_rows: X <- X M (transpose 0: M = Rinv) or
+// X <- X M^T (transpose 1: M = R) on rows of J values.  launch_qr_core: Gout = G x_n R on the
+// padded core.
+int qr_gram_ctas(int64_t rows, int num_sms);
+cudaError_t launch_qr_factor(const float* U, int64_t rows, int ld, int J, int grid, double* parts,
+                             double* R, double* Rinv, double* R1, double* R1inv, int* bad,
+                             cudaStream_t s);
+cudaError_t launch_qr_rows(float* X, int64_t rows, int ld, int J, const double* M, int transpose,
+                           cudaStream_t s);
+cudaError_t launch_qr_core(const float* G, float* Gout, int N, int JP, int ldg, int n, int J,
+                           const double* R, cudaStream_t s);
 
 }  // namespace s3

@@ -31,9 +31,12 @@ struct SegOut {
 
 // worker: groups [g0, g1)
 void sort_groups(const HostInput& in, HostGrouping& G, int64_t g0, int64_t g1,
-                 std::vector<SegOut>& segs, std::vector<std::vector<int64_t>>& nseg_per_group) {
+                 std::vector<SegOut>& segs, std::vector<std::vector<int64_t>>& nseg_per_group,
+                 std::vector<std::vector<int64_t>>& nlong_per_group,
+                 std::vector<std::vector<int64_t>>& nhuge_per_group) {
     const int N = in.N, M = in.M, nF = N + M;
     std::vector<std::pair<int32_t, int32_t>> ev;
+    SegOut tmp;
     for (int64_t g = g0; g < g1; ++g) {
         const int64_t t0 = G.t_off[(size_t)g], t1 = G.t_off[(size_t)g + 1];
         for (int F = 0; F < nF; ++F) {
@@ -87,6 +90,33 @@ void sort_groups(const HostInput& in, HostGrouping& G, int64_t g0, int64_t g1,
                 p = q;
             }
             nseg_per_group[(size_t)F][(size_t)(g - g0)] = nseg;
+            // huge, then long segments to the front (slot positions do not depend on the
+            // order of segments)
+            int64_t nlong = 0, nhuge = 0;
+            if (G.pos_kind == POS_SLOT && G.long_thr > 0) {
+                SegOut& so = segs[(size_t)F];
+                const size_t s0 = so.row.size() - (size_t)nseg;
+                tmp.row.assign(so.row.begin() + (std::ptrdiff_t)s0, so.row.end());
+                tmp.start.assign(so.start.begin() + (std::ptrdiff_t)s0, so.start.end());
+                tmp.cnt.assign(so.cnt.begin() + (std::ptrdiff_t)s0, so.cnt.end());
+                auto cls = [&](int32_t cnt) {
+                    return (G.huge_thr > 0 && cnt > G.huge_thr) ? 2 : cnt > G.long_thr ? 1 : 0;
+                };
+                size_t w = s0;
+                for (int want = 2; want >= 0; --want)
+                    for (size_t i = 0; i < tmp.row.size(); ++i) {
+                        const int k = cls(tmp.cnt[i]);
+                        if (k != want) continue;
+                        so.row[w] = tmp.row[i];
+                        so.start[w] = tmp.start[i];
+                        so.cnt[w] = tmp.cnt[i];
+                        ++w;
+                        nlong += k >= 1;
+                        nhuge += k == 2;
+                    }
+            }
+            nhuge_per_group[(size_t)F][(size_t)(g - g0)] = nhuge;
+            nlong_per_group[(size_t)F][(size_t)(g - g0)] = nlong;
         }
     }
 }
@@ -94,10 +124,13 @@ void sort_groups(const HostInput& in, HostGrouping& G, int64_t g0, int64_t g1,
 }  // namespace
 
 std::string build_grouping(const HostInput& in, const int64_t* order, int64_t n_union, int rule,
-                           int64_t size, int pos_kind, HostGrouping& G) {
+                           int64_t size, int pos_kind, HostGrouping& G, int long_thr,
+                           int huge_thr) {
     const int N = in.N, M = in.M, nF = N + M;
     G = HostGrouping();
     G.pos_kind = pos_kind;
+    G.long_thr = long_thr;
+    G.huge_thr = huge_thr;
     G.nF = nF;
     if (size <= 0) return "group size must be positive";
     // item -> (matrix, local index)
@@ -186,14 +219,17 @@ std::string build_grouping(const HostInput& in, const int64_t* order, int64_t n_
     std::vector<int64_t> bpos((size_t)nblk + 1);
     for (int64_t b = 0; b <= nblk; ++b) bpos[(size_t)b] = ng * b / nblk;
     std::vector<std::vector<SegOut>> segs((size_t)nblk, std::vector<SegOut>((size_t)nF));
-    std::vector<std::vector<std::vector<int64_t>>> nsg((size_t)nblk);
+    std::vector<std::vector<std::vector<int64_t>>> nsg((size_t)nblk), nlg((size_t)nblk), nhg((size_t)nblk);
     std::atomic<int64_t> next{0};
     auto worker = [&]() {
         for (;;) {
             const int64_t b = next.fetch_add(1);
             if (b >= nblk) break;
             nsg[(size_t)b].assign((size_t)nF, std::vector<int64_t>((size_t)(bpos[(size_t)b + 1] - bpos[(size_t)b])));
-            sort_groups(in, G, bpos[(size_t)b], bpos[(size_t)b + 1], segs[(size_t)b], nsg[(size_t)b]);
+            nlg[(size_t)b] = nsg[(size_t)b];
+            nhg[(size_t)b] = nsg[(size_t)b];
+            sort_groups(in, G, bpos[(size_t)b], bpos[(size_t)b + 1], segs[(size_t)b], nsg[(size_t)b],
+                        nlg[(size_t)b], nhg[(size_t)b]);
         }
     };
     std::vector<std::thread> th;
@@ -203,6 +239,8 @@ std::string build_grouping(const HostInput& in, const int64_t* order, int64_t n_
     for (int F = 0; F < nF; ++F) {
         G.seg_off[F].assign((size_t)ng + 1, 0);
         G.slot_off[F].assign((size_t)ng + 1, 0);
+        G.seg_nlong[F].assign((size_t)ng, 0);
+        G.seg_nhuge[F].assign((size_t)ng, 0);
         size_t total = 0;
         for (int64_t b = 0; b < nblk; ++b) total += segs[(size_t)b][(size_t)F].row.size();
         G.seg_row[F].reserve(total);
@@ -216,6 +254,8 @@ std::string build_grouping(const HostInput& in, const int64_t* order, int64_t n_
             for (int64_t g = bpos[(size_t)b]; g < bpos[(size_t)b + 1]; ++g) {
                 const int64_t ns = nsg[(size_t)b][(size_t)F][(size_t)(g - bpos[(size_t)b])];
                 G.seg_off[F][(size_t)g + 1] = G.seg_off[F][(size_t)g] + ns;
+                G.seg_nlong[F][(size_t)g] = (int32_t)nlg[(size_t)b][(size_t)F][(size_t)(g - bpos[(size_t)b])];
+                G.seg_nhuge[F][(size_t)g] = (int32_t)nhg[(size_t)b][(size_t)F][(size_t)(g - bpos[(size_t)b])];
                 G.max_seg[F] = std::max(G.max_seg[F], ns);
             }
         }

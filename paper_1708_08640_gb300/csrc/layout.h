@@ -36,6 +36,9 @@ enum PosKind {
 
 struct HostGrouping {
     int pos_kind = POS_SLOT;
+    int long_thr = 0;          // > 0 (POS_SLOT only): each group lists its segments of more than
+    int huge_thr = 0;          // huge_thr events first, then those of more than long_thr, then
+                               // the others, each class in row order (huge_thr 0: no huge class)
     int64_t ngroups = 0;
     int nF = 0;
     std::vector<int64_t> t_off;
@@ -50,6 +53,8 @@ struct HostGrouping {
     std::vector<int64_t> c_src[8];
     std::vector<int64_t> seg_off[12], slot_off[12];
     std::vector<int32_t> seg_row[12], seg_start[12], seg_cnt[12];
+    std::vector<int32_t> seg_nlong[12];   // [groups] segments of more than long_thr events
+    std::vector<int32_t> seg_nhuge[12];   // [groups] segments of more than huge_thr events
     int64_t max_t = 0;
     int64_t max_c[8] = {};
     int64_t max_seg[12] = {};
@@ -58,8 +63,10 @@ struct HostGrouping {
 
 // order: n_union items (nullptr = identity order).  Items k < nnz are tensor entries,
 // then the entries of coupled matrix 0, 1, ...  Returns an empty string on success.
+// long_thr, huge_thr: see HostGrouping.
 std::string build_grouping(const HostInput& in, const int64_t* order, int64_t n_union, int rule,
-                           int64_t size, int pos_kind, HostGrouping& out);
+                           int64_t size, int pos_kind, HostGrouping& out, int long_thr = 0,
+                           int huge_thr = 0);
 
 // The visiting order derived from a seed: items sorted by a counter-based 64-bit key
 // (splitmix64 of seed and item, stream 63), ties by item.

@@ -90,6 +90,47 @@ __device__ __forceinline__ float partials3(const float* __restrict__ sG, const f
     return xt;
 }
 
+// The same sweep for one of L lanes that share an entry: this lane takes the JH = JP/L
+// (rounded up) values of j1 starting at j1base and gets p1 for those, and its parts of p2, p3
+// and x~ (the lanes add their parts).  a1s holds a1[j1base .. j1base + JH), zero past JP.
+template <int JP, int L>
+__device__ __forceinline__ float partials3_lane(const float* __restrict__ sG, int j1base,
+                                                const float (&a1s)[(JP + L - 1) / L],
+                                                const float (&a2)[JP], const float (&a3)[JP],
+                                                float (&p1s)[(JP + L - 1) / L], float (&p2)[JP],
+                                                float (&p3)[JP]) {
+    constexpr int JPR = round4(JP);
+    constexpr int JH = (JP + L - 1) / L;
+    constexpr int U1 = JH <= 12 ? JH : 1;
+#pragma unroll
+    for (int j = 0; j < JP; ++j) { p2[j] = 0.f; p3[j] = 0.f; }
+#pragma unroll U1
+    for (int jj = 0; jj < JH; ++jj) {
+        const int j1 = min(j1base + jj, JP - 1);   // past JP, a1s is zero
+        const float a1j = a1s[jj];
+        float p1j = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < JP; ++j2) {
+            float g[JP];
+            load_grow<JP>(sG + (j1 * JP + j2) * JPR, g);
+            const float w = a1j * a2[j2];
+            float t = 0.f;
+#pragma unroll
+            for (int j3 = 0; j3 < JP; ++j3) {
+                t = fmaf(g[j3], a3[j3], t);
+                p3[j3] = fmaf(g[j3], w, p3[j3]);
+            }
+            p1j = fmaf(t, a2[j2], p1j);
+            p2[j2] = fmaf(t, a1j, p2[j2]);
+        }
+        p1s[jj] = p1j;
+    }
+    float xt = 0.f;
+#pragma unroll
+    for (int jj = 0; jj < JH; ++jj) xt = fmaf(a1s[jj], p1s[jj], xt);
+    return xt;
+}
+
 // prediction only: x~ = sum_j1 a1 sum_j2 a2 sum_j3 g a3
 template <int JP>
 __device__ __forceinline__ float predict3(const float* __restrict__ sG, const float (&a1)[JP],
@@ -190,7 +231,8 @@ __device__ __forceinline__ float predict4(const float* __restrict__ sG, const fl
 // Thread t owns multi-indices q over the first N-1 modes and all JP values of the last
 // mode; when there are fewer multi-indices than threads the entries are split into KS
 // slices.  Running sums are Neumaier-compensated across tiles.
-template <int N, int JP>
+// ST: rows between the stage's per-mode blocks (at least the entries of a tile)
+template <int N, int JP, int ST = kTile>
 struct CoreAcc {
     static constexpr int JPR = round4(JP);
     static constexpr int Q = ipow_t<JP, N - 1>::v;
@@ -206,7 +248,7 @@ struct CoreAcc {
             for (int j = 0; j < JP; ++j) { s[k][j] = 0.f; c[k][j] = 0.f; }
     }
 
-    // stage: shared memory [N][kTile][JPR]; nb valid entries
+    // stage: shared memory [N][ST][JPR]; nb valid entries
     __device__ __forceinline__ void add_tile(const float* __restrict__ stage, int nb) {
         const int t = threadIdx.x;
         const int slice = KS > 1 ? t / Q : 0;
@@ -224,11 +266,11 @@ struct CoreAcc {
 #pragma unroll
             for (int j = 0; j < JP; ++j) tile[j] = 0.f;
             for (int b = slice; b < nb; b += KS) {
-                float w = stage[(0 * kTile + b) * JPR + jj[0]];
+                float w = stage[(0 * ST + b) * JPR + jj[0]];
 #pragma unroll
-                for (int n = 1; n < N - 1; ++n) w *= stage[(n * kTile + b) * JPR + jj[n]];
+                for (int n = 1; n < N - 1; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
                 float r[JP];
-                load_grow<JP>(stage + ((N - 1) * kTile + b) * JPR, r);
+                load_grow<JP>(stage + ((N - 1) * ST + b) * JPR, r);
 #pragma unroll
                 for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
             }
@@ -276,7 +318,7 @@ struct CoreAcc {
 // One tile's core step added lock-free to the core in global memory: thread (q, slice) sums
 // its slice of the tile's entries for multi-index q and all JP values of the last mode, then
 // adds  sc * sum - rg * G  (rg only once, by slice 0) with atomics.
-template <int N, int JP>
+template <int N, int JP, int ST = kTile>
 struct CoreTile {
     static constexpr int JPR = round4(JP);
     static constexpr int Q = ipow_t<JP, N - 1>::v;
@@ -302,11 +344,11 @@ struct CoreTile {
 #pragma unroll
             for (int j = 0; j < JP; ++j) tile[j] = 0.f;
             for (int b = slice; b < nb; b += KS) {
-                float w = stage[(0 * kTile + b) * JPR + jj[0]];
+                float w = stage[(0 * ST + b) * JPR + jj[0]];
 #pragma unroll
-                for (int n = 1; n < N - 1; ++n) w *= stage[(n * kTile + b) * JPR + jj[n]];
+                for (int n = 1; n < N - 1; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
                 float r[JP];
-                load_grow<JP>(stage + ((N - 1) * kTile + b) * JPR, r);
+                load_grow<JP>(stage + ((N - 1) * ST + b) * JPR, r);
 #pragma unroll
                 for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
             }
@@ -322,5 +364,28 @@ struct CoreTile {
         }
     }
 };
+
+// the N partial products and the prediction of one entry (3- or 4-way)
+template <int N, int JP>
+__device__ __forceinline__ float entry_partials(const float* sG, float (&a)[N][JP],
+                                                float (&p)[N][JP]) {
+    if constexpr (N == 3) return partials3<JP>(sG, a[0], a[1], a[2], p[0], p[1], p[2]);
+    else return partials4<JP>(sG, a[0], a[1], a[2], a[3], p[0], p[1], p[2], p[3]);
+}
+
+template <int N, int JP>
+__device__ __forceinline__ float entry_predict(const float* sG, float (&a)[N][JP]) {
+    if constexpr (N == 3) return predict3<JP>(sG, a[0], a[1], a[2]);
+    else return predict4<JP>(sG, a[0], a[1], a[2], a[3]);
+}
+
+// the opt-in above 48 KB counts static shared memory too, so set the limit whenever the
+// dynamic part is large
+template <typename K>
+static inline cudaError_t prep(K kernel, size_t smem) {
+    if (smem > 32 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaSuccess;
+}
 
 }  // namespace s3

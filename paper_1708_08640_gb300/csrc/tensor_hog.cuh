@@ -1,0 +1,287 @@
+// The FP32 HOGWILD tensor kernel (sm_103a, CUDA cores), shared by the translation units
+// that compile its variants (k_tensor_hog2.cu: two lanes per entry; k_tensor_hog4.cu: four
+// lanes, and the 4-way one-lane form).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hog_common.cuh"
+#include "kernels.h"
+#include "tensor_fp32.cuh"
+
+namespace s3 {
+
+// ------------------------------------------------------------------ HOGWILD
+// One persistent launch per epoch.  CTAs claim tiles in visiting order from a global
+// counter; a tile reads the current rows and core (coherent loads: other CTAs update them
+// concurrently), writes its row gradients to slots in shared memory, sums every row's slots
+// and adds the row steps with vector atomics, and adds its share of the core step to G
+// (lock-free, like the rows).
+// L adjacent lanes share an entry (3-way: the j1 range is split, the lanes' parts of p2, p3
+// and x~ are added with shuffles), so a tile holds kTile / L entries: fewer entries in flight
+// (less staleness) for the same number of threads.
+// A CTA has kTile compute threads and one prefetch warp.  While the compute threads work on
+// a tile, the prefetch warp claims the next tile and loads everything it will read besides
+// the parameters (indices, values, slot positions, coupled entries, segment table) into the
+// other metadata buffer, so that a tile's critical path starts at its row gathers; the core
+// is re-read at the start of every tile, while those gathers are in flight.
+constexpr int kHogThreads = kTile + 32;
+
+template <int N, int JP>
+struct HogCore {
+    static constexpr int Q = ipow_t<JP, N - 1>::v;
+    static constexpr int floats = Q * round4(JP);
+};
+
+__device__ __forceinline__ void compute_barrier() {
+    asm volatile("bar.sync 1, %0;" :: "r"(kTile) : "memory");
+}
+
+// two CTAs per SM for padded ranks up to 16 (at most 112 registers a thread), one above
+template <int N, int JP, int L>
+__global__ void __launch_bounds__(kHogThreads, (JP <= 16 ? 2 : 1))
+k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
+                                                            int* tile_counter, const float* eta_p,
+                                                            int row_mean, float core_step_scale,
+                                                            HogSmem H) {
+    static_assert(L == 1 || N == 3, "lanes per entry > 1 is built for 3-way tensors");
+    constexpr int JPR = round4(JP);
+    constexpr int JH = (JP + L - 1) / L;
+    constexpr int ST = kTile / L;          // entries per tile at most: rows per stage block
+    constexpr int GF = HogCore<N, JP>::floats;
+    // coupled rows of the first round are gathered together with the tensor rows when they
+    // fit in the registers
+    constexpr bool kEarlyCpl = JP <= 10;
+    extern __shared__ __align__(16) float smem[];
+    float* sG = smem;                  // the core (see hog_layout)
+    float* stage = smem + GF;
+    const float eta = *eta_p;
+    const int tid = threadIdx.x;
+    const bool pf = tid >= kTile;          // the prefetch warp
+    const int lane = tid & 31;
+    const int slot = tid / L, lsub = tid % L;
+    int* meta_base = reinterpret_cast<int*>(smem);
+    // the first tile
+    if (pf) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(tile_counter, 1);
+        t0 = __shfl_sync(0xffffffffu, t0, 0);
+        hog_prefetch<N>(P, Gr, t0, n_tiles, meta_base + H.meta[0], H, ST, lane);
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int b = it & 1;
+        const int* mb = meta_base + H.meta[b];
+        const int64_t t = *reinterpret_cast<const int64_t*>(mb + kMetaTile);
+        if (t >= n_tiles) break;
+        if (pf) {
+            int nx = 0;
+            if (lane == 0) nx = atomicAdd(tile_counter, 1);
+            nx = __shfl_sync(0xffffffffu, nx, 0);
+            hog_prefetch<N>(P, Gr, nx, n_tiles, meta_base + H.meta[b ^ 1], H, ST, lane);
+        } else {
+            // the current core (coherent: other CTAs add to it), once the tile's row gathers
+            // are in flight
+            auto reload_core = [&]() {
+                for (int l = tid * 4; l < GF; l += kTile * 4) st4(sG + l, ld4_cg(P.G + l));
+                compute_barrier();
+            };
+            const int nb = mb[kMetaNb];
+            const int nc = mb[kMetaNc];
+            const HogMeta& M = H.M;
+            // the first round of coupled entries: indices from the buffer, rows gathered now
+            const bool hc = kEarlyCpl && tid < nc;
+            float cu[kEarlyCpl ? JP : 1], cv[kEarlyCpl ? JP : 1];
+            int cm = 0, ck = 0;
+            if constexpr (kEarlyCpl) {
+                if (hc) {
+                    cm = mb[M.c_m + tid];
+                    ck = mb[M.c_k + tid];
+                    load_row<JP, true>(P.U[P.cmode[cm]] + (int64_t)mb[M.c_r + tid] * JPR, cu);
+                    load_row<JP, true>(P.V[cm] + (int64_t)ck * JPR, cv);
+                }
+            }
+            if constexpr (L == 1) {
+                float a[N][JP];
+                int32_t row[N];
+                if (tid < nb) {
+#pragma unroll
+                    for (int n = 0; n < N; ++n) {
+                        row[n] = mb[M.tidx + n * ST + tid];
+                        load_row<JP, true>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
+                    }
+                }
+                reload_core();
+                if (tid < nb) {
+                    float p[N][JP];
+                    const float err = __int_as_float(mb[M.tval + tid]) - entry_partials<N, JP>(sG, a, p);
+#pragma unroll
+                    for (int n = 0; n < N; ++n) {
+                        const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                        float c[JPR];
+#pragma unroll
+                        for (int j = 0; j < JPR; ++j) c[j] = j < JP ? fmaf(-err, p[n][j], r * a[n][j]) : 0.f;
+                        put_slot<JPR>(smem, H, n, mb[M.tpos + n * ST + tid], c);
+                        float* sp = stage + (n * ST + tid) * JPR;
+#pragma unroll
+                        for (int j = 0; j < JP; ++j) sp[j] = n == 0 ? err * a[n][j] : a[n][j];
+                    }
+                }
+            } else {
+                // every lane runs the shuffles, so invalid slots work on zero rows
+                const bool valid = slot < nb;
+                const int sl = valid ? slot : 0;
+                int32_t row[3] = {0, 0, 0};
+                float a1s[JH], a2[JP], a3[JP];
+                float x = 0.f;
+                const int j1base = lsub * JH;
+                if (valid) {
+#pragma unroll
+                    for (int n = 0; n < 3; ++n) row[n] = mb[M.tidx + n * ST + sl];
+                    const float* u1 = P.U[0] + (int64_t)row[0] * JPR;
+#pragma unroll
+                    for (int jj = 0; jj < JH; ++jj) a1s[jj] = j1base + jj < JP ? __ldcg(u1 + j1base + jj) : 0.f;
+                    load_row<JP, true>(P.U[1] + (int64_t)row[1] * JPR, a2);
+                    load_row<JP, true>(P.U[2] + (int64_t)row[2] * JPR, a3);
+                    x = __int_as_float(mb[M.tval + sl]);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < JH; ++jj) a1s[jj] = 0.f;
+#pragma unroll
+                    for (int j = 0; j < JP; ++j) { a2[j] = 0.f; a3[j] = 0.f; }
+                }
+                reload_core();
+                float p1s[JH], p2[JP], p3[JP];
+                float xt = partials3_lane<JP, L>(sG, j1base, a1s, a2, a3, p1s, p2, p3);
+#pragma unroll
+                for (int o = 1; o < L; o <<= 1) {
+                    xt += __shfl_xor_sync(0xffffffffu, xt, o);
+#pragma unroll
+                    for (int j = 0; j < JP; ++j) {
+                        p2[j] += __shfl_xor_sync(0xffffffffu, p2[j], o);
+                        p3[j] += __shfl_xor_sync(0xffffffffu, p3[j], o);
+                    }
+                }
+                if (valid) {
+                    const float err = x - xt;
+                    // mode 1: this lane's j1 values (the slot's padding is written by the last lane)
+                    {
+                        const float r = P.lambda_reg * __ldg(P.inv_cnt[0] + row[0]);
+                        float* sa = smem + H.off[0] + mb[M.tpos + sl] * slot_stride(JPR);
+                        float* sp = stage + (0 * ST + slot) * JPR;
+#pragma unroll
+                        for (int jj = 0; jj < JH; ++jj) {
+                            const int j1 = j1base + jj;
+                            if (j1 < JP) {
+                                sa[j1] = fmaf(-err, p1s[jj], r * a1s[jj]);
+                                sp[j1] = err * a1s[jj];
+                            }
+                        }
+                        if (lsub == L - 1)
+#pragma unroll
+                            for (int j = JP; j < JPR; ++j) sa[j] = 0.f;
+                    }
+                    // modes 2 and 3: lanes 0 and 1 write one each (every lane holds the whole
+                    // p2 and p3)
+                    if (lsub < 2) {
+                        // (element-wise selects: a pointer to either register array would move
+                        // both arrays to local memory)
+                        const int n = 1 + lsub;
+                        const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                        float c[JPR];
+                        float* sp = stage + (n * ST + slot) * JPR;
+#pragma unroll
+                        for (int j = 0; j < JPR; ++j) {
+                            const float pj = lsub == 0 ? p2[j < JP ? j : 0] : p3[j < JP ? j : 0];
+                            const float aj = lsub == 0 ? a2[j < JP ? j : 0] : a3[j < JP ? j : 0];
+                            c[j] = j < JP ? fmaf(-err, pj, r * aj) : 0.f;
+                            if (j < JP) sp[j] = aj;
+                        }
+                        put_slot<JPR>(smem, H, n, mb[M.tpos + n * ST + sl], c);
+                    }
+                }
+            }
+            // coupled entries, Eq. (8): the first round from the rows gathered above, then
+            // any further rounds in full
+            if constexpr (kEarlyCpl) {
+                if (hc) hog_coupled_one<JP>(P, smem, H, cm, ck, mb[M.c_pu + tid], mb[M.c_pv + tid],
+                                            __int_as_float(mb[M.c_y + tid]), cu, cv);
+            }
+            for (int e = kEarlyCpl ? tid + kTile : tid; e < nc; e += kTile) {
+                float u[JP], v[JP];
+                const int m = mb[M.c_m + e], k = mb[M.c_k + e];
+                load_row<JP, true>(P.U[P.cmode[m]] + (int64_t)mb[M.c_r + e] * JPR, u);
+                load_row<JP, true>(P.V[m] + (int64_t)k * JPR, v);
+                hog_coupled_one<JP>(P, smem, H, m, k, mb[M.c_pu + e], mb[M.c_pv + e],
+                                    __int_as_float(mb[M.c_y + e]), u, v);
+            }
+            compute_barrier();
+            // core: this tile's share of the core step,
+            //   G += eta * cs / W * (sum_b e_b a1 o..o aN / n_t - lambda_reg / |Omega| * G)
+            if (nb > 0) {
+                const float sc = eta * core_step_scale / (float)nb;
+                const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
+                CoreTile<N, JP, ST>::apply(stage, nb, sG, P.G, sc, rg);
+            }
+            hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kTile);
+        }
+        __syncthreads();
+    }
+}
+
+static inline size_t hog_core_floats(int N, int JP) {
+    size_t q = 1;
+    for (int n = 0; n < N - 1; ++n) q *= JP;
+    return q * round4(JP);
+}
+
+// the HOGWILD kernel's fixed shared memory (floats): the core and a stage of kTile / L rows
+// per mode
+static inline size_t hog_fixed_floats(int N, int JP, int L) {
+    return hog_core_floats(N, JP) + (size_t)N * (kTile / L) * round4(JP);
+}
+
+// the whole layout: core, stage, slots, metadata buffers
+static inline size_t hog_layout(int N, int JP, int L, const int64_t* max_events,
+                                const int64_t* max_segs, int64_t ccap, int nF, HogSmem* H) {
+    return hog_meta_smem_floats(round4(JP), N, kTile / L, max_events, max_segs, ccap, nF, H,
+                                hog_fixed_floats(N, JP, L));
+}
+
+// launcher and occupancy query over a list of (N, JP, L) variants, for one translation unit
+#define S3_DEFINE_HOG_VARIANTS(SHAPES, LAUNCH_NAME, BLOCKS_NAME)                                 \
+    cudaError_t LAUNCH_NAME(int N, int JP, int L, const DParams& P, const DGroup& G,              \
+                            int64_t n_tiles, int* tile_counter, int grid, const float* eta,       \
+                            int row_mean, float core_step_scale, const int64_t* max_events,       \
+                            const int64_t* max_segs, int64_t ccap, cudaStream_t s) {              \
+        if (n_tiles <= 0) return cudaSuccess;                                                     \
+        HogSmem H{};                                                                              \
+        const size_t smem = hog_layout(N, JP, L, max_events, max_segs, ccap, P.N + P.M, &H) *     \
+                            sizeof(float);                                                        \
+        SHAPES(S3_HOG_LAUNCH_ONE)                                                                 \
+        return cudaErrorInvalidValue;                                                             \
+    }                                                                                             \
+    int BLOCKS_NAME(int N, int JP, int L, size_t smem) {                                          \
+        int nb = 0;                                                                               \
+        SHAPES(S3_HOG_BLOCKS_ONE)                                                                 \
+        return 0;                                                                                 \
+    }
+
+#define S3_HOG_LAUNCH_ONE(NN, JJ, LL)                                                          \
+    if (N == NN && JP == JJ && L == LL) {                                                      \
+        cudaError_t e = prep(k_tensor_hog<NN, JJ, LL>, smem);                                  \
+        if (e != cudaSuccess) return e;                                                        \
+        k_tensor_hog<NN, JJ, LL><<<grid, kHogThreads, smem, s>>>(P, G, n_tiles, tile_counter, eta, \
+                                                           row_mean, core_step_scale, H);      \
+        return cudaGetLastError();                                                             \
+    }
+
+#define S3_HOG_BLOCKS_ONE(NN, JJ, LL)                                                          \
+    if (N == NN && JP == JJ && L == LL) {                                                      \
+        if (prep(k_tensor_hog<NN, JJ, LL>, smem) != cudaSuccess) return 0;                     \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tensor_hog<NN, JJ, LL>, kHogThreads, \
+                                                          smem) != cudaSuccess)                \
+            return 0;                                                                          \
+        return nb;                                                                             \
+    }
+
+}  // namespace s3

@@ -40,7 +40,8 @@ class S3CMTF:
 
     def __init__(self, dims, J, train_idx, train_val, coupled=(), *, lr0=0.01, mu=0.1,
                  lambda_reg=0.01, lambda_m=1.0, batch=4096, core_scale=1.0, row_rule="sum",
-                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, seed=0, order=None, device=None,
+                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, seed=0, order=None,
+                 device=None,
                  stream=None):
         self.lib = L.load()
         self.device = torch.device(device if device is not None else "cuda")
@@ -71,7 +72,7 @@ class S3CMTF:
                                     None if v is None else v.ctypes.data)
         hp = L.s3_hparams(lr0, mu, lambda_reg, lambda_m, int(batch), core_scale,
                           _ROW[row_rule] if isinstance(row_rule, str) else int(row_rule),
-                          int(hog_tile), float(hog_staleness), int(hog_ctas))
+                          int(hog_tile), float(hog_staleness), int(hog_ctas), int(mb_ctas))
         Jarr = (C.c_int * self.N)(*self.J)
         order_arr = None if order is None else _host(order, np.int64)
         with torch.cuda.device(self.device):
@@ -231,6 +232,21 @@ class S3CMTF:
         a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(self.lib.s3_info(self.ctx, C.byref(a), C.byref(b), C.byref(c)))
         return dict(n_union=a.value, n_batches=b.value, n_tiles=c.value)
+
+    def finalize_qr(self):
+        """Algorithm 1's final step: orthonormal factors, the core and coupled factors
+        transformed so that every prediction stays the same."""
+        self._enter()
+        self._check(self.lib.s3_finalize_qr(self.ctx))
+        self._leave()
+
+    def hog_config(self, precision="fp32"):
+        """The HOGWILD launch of a precision form: CTAs, entries per tile, dynamic shared
+        memory per CTA, CTAs per SM (ctas x tile = entries in flight)."""
+        v = [C.c_int64() for _ in range(4)]
+        self._check(self.lib.s3_hog_config(self.ctx, _PREC[precision], *[C.byref(x) for x in v]))
+        return dict(ctas=v[0].value, tile=v[1].value, smem_bytes=v[2].value,
+                    ctas_per_sm=v[3].value)
 
     def update_values(self, x_val, y_vals=None):
         """x_val / y_vals: host float32 arrays (pinned torch tensors or numpy), in the order

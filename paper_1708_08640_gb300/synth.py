@@ -222,13 +222,33 @@ def _cfg0(rng, noise=0.1):
     return dims, J, tr_i, tr_v, te_i, te_v, cpl, hp, rec
 
 
+def rating_core_scale(J):
+    """Core step scale of the rating workloads: 32 at ranks (10, 10, 10), times (10^3 / prod J)
+    at other ranks.  With factors ~ U(0,1) the outer products a1 o a2 o a3 share a mean
+    direction of squared norm prod(J_n / 4), which sets the curvature of a mean core step; the
+    scaling keeps eta * core_scale * prod(J_n / 4) at its rank-10 value (0.5 at eta 0.001),
+    where rank 32 with core_scale 32 diverges."""
+    return 32.0 * 1000.0 / float(np.prod(J))
+
+
+def with_rank(prob, J):
+    """A copy of a rating-workload problem at ranks J (cfg2: the cfg1 data at J = 16, 32),
+    with the core step scale of that rank."""
+    import copy
+    q = copy.copy(prob)
+    q.J = tuple(int(j) for j in J)
+    q.hparams = dict(prob.hparams, core_scale=rating_core_scale(q.J))
+    return q
+
+
 def _rating_like(rng, dims, nnz, J, n_cpl, zipf="zipf1.1"):
     coords, v, _, _ = _tensor(rng, dims, nnz, (zipf, zipf, "uniform"), (10, 10, 10),
                               "rating", 0.2)
     tr_i, tr_v, te_i, te_v = _split(rng, coords, v, 0.10)
     r, c, y = _binary_symmetric(rng, n_cpl, dims[0], zipf)
     cpl = [Coupled(0, dims[0], r, c, y)]
-    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=10.0, batch=4096, core_scale=32.0)
+    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=10.0, batch=4096,
+              core_scale=rating_core_scale(J))
     rec = (f"3-way {dims[0]}x{dims[1]}x{dims[2]}, {nnz} unique coordinates, modes 1-2 "
            f"{zipf}, mode 3 uniform; planted rank-(10,10,10) core ~ N(0,1), factors ~ U(0,1), "
            "standardised to mean 3 std 1, + N(0,0.2^2), rounded half-even, clipped to 1..5; "

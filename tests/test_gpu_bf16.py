@@ -17,9 +17,11 @@ from tests.oracle_cases import random_problem
 pytestmark = pytest.mark.gpu
 
 
-def one_tile_problem(J, seed=4):
-    prob, params = random_problem((30, 20, 10), (J, J, J), nnz=200, n_coupled=1, seed=seed,
-                                  coupled_nnz=60, K=9)
+def one_tile_problem(J, seed=4, nnz=120):
+    # 120 entries: one tile of the FP32 kernel (128 entries, two lanes each) and of the
+    # BF16 kernel (128 entries); 60 entries: one tile of 64 (four lanes each)
+    prob, params = random_problem((30, 20, 10), (J, J, J), nnz=nnz, n_coupled=1, seed=seed,
+                                  coupled_nnz=nnz // 3, K=9)
     prob.train_val = f32(prob.train_val + 2.0)
     for c in prob.coupled:
         c.vals = f32(c.vals)
@@ -28,14 +30,15 @@ def one_tile_problem(J, seed=4):
     return prob, fp32_params((G, U, V))
 
 
-def run_one_tile(prob, params, precision, lr0=0.01):
+def run_one_tile(prob, params, precision, lr0=0.01, tile=128):
     from paper_1708_08640_gb300.model import S3CMTF
     hp = dict(lr0=lr0, mu=0.0, lambda_reg=0.1, lambda_m=2.0, core_scale=1.0)
     cpl = [(c.mode, c.K, c.rows, c.cols, c.vals) for c in prob.coupled]
-    # no staleness scaling: with one tile nothing is stale, and the oracle's group step is
-    # the plain one
+    # one tile (128 entries: the FP32 kernel's largest, on two lanes) on one CTA (the BF16
+    # form's tile then holds the same 128) and no staleness scaling: with one tile nothing
+    # is stale, and the oracle's group step is the plain one
     gpu = S3CMTF(prob.dims, prob.J, prob.train_idx, prob.train_val, cpl, hog_staleness=-1.0,
-                 **hp)
+                 hog_tile=tile, hog_ctas=1, **hp)
     gpu.set_params(*params)
     gpu.epoch("hogwild", precision)
     G, U, V = gpu.get_params()
@@ -46,12 +49,13 @@ def run_one_tile(prob, params, precision, lr0=0.01):
     return (G, U, V), orc
 
 
-@pytest.mark.parametrize("J", [5, 16])
-def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J):
+@pytest.mark.parametrize("J,tile,nnz", [(5, 128, 120), (16, 128, 120), (10, 64, 60)])
+def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J, tile, nnz):
     """1e-4 for the core: the HOGWILD kernel sums a tile's core gradients in plain FP32 (the
-    minibatch kernels compensate theirs); 1e-5 for the rows."""
-    prob, params = one_tile_problem(J)
-    (G, U, V), orc = run_one_tile(prob, params, "fp32")
+    minibatch kernels compensate theirs); 1e-5 for the rows.  Tiles of 128 entries run two
+    lanes per entry, tiles of 64 four."""
+    prob, params = one_tile_problem(J, nnz=nnz)
+    (G, U, V), orc = run_one_tile(prob, params, "fp32", tile=tile)
     G0, U0, V0 = params
     assert_step_close(G.cpu().double().numpy(), orc.G, G0, 1e-4, "G")
     for n in range(3):
@@ -59,8 +63,10 @@ def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J):
     assert_step_close(V[0].cpu().double().numpy(), orc.V[0], V0[0], 1e-5, "V")
 
 
-def test_bf16_hogwild_single_tile_step(cuda_lib):
-    prob, params = one_tile_problem(16)
+@pytest.mark.parametrize("J", [16, 24])
+def test_bf16_hogwild_single_tile_step(cuda_lib, J):
+    """J = 16: padded rank 16; J = 24: padded rank 32 with zero padding in every operand."""
+    prob, params = one_tile_problem(J)
     (G, U, V), orc = run_one_tile(prob, params, "bf16")
     G0, U0, V0 = params
     errs = {}
@@ -74,14 +80,17 @@ def test_bf16_hogwild_single_tile_step(cuda_lib):
     assert max(errs.values()) < 3e-2, errs
 
 
-def test_bf16_rmse_tracks_fp32_on_rating_tensor(cuda_lib):
-    """cfg2 data at J = 16 (the cfg1 rating tensor): the BF16 form's test RMSE per epoch
-    within 1% of the FP32 form's (both HOGWILD, same data, start and order)."""
-    import copy
+@pytest.fixture(scope="module")
+def rating_tensor():
+    return synth.make_problem("cfg1")
+
+
+@pytest.mark.parametrize("J", [16, 32])
+def test_bf16_rmse_tracks_fp32_on_rating_tensor(cuda_lib, rating_tensor, J):
+    """cfg2 data at J = 16 and 32 (the cfg1 rating tensor): the BF16 form's test RMSE per
+    epoch within 1% of the FP32 form's (both HOGWILD, same data, start and order)."""
     from paper_1708_08640_gb300.model import S3CMTF
-    p = synth.make_problem("cfg1")
-    q = copy.copy(p)
-    q.J = (16, 16, 16)
+    q = synth.with_rank(rating_tensor, (J, J, J))
     init = synth.init_params(q, 1)
     order = synth.union_order(q, 2)
     curves = {}
@@ -91,7 +100,10 @@ def test_bf16_rmse_tracks_fp32_on_rating_tensor(cuda_lib):
         m.set_test(q.test_idx, q.test_val)
         out = []
         for t in range(3):
-            m.epoch("hogwild", prec)
+            try:
+                m.epoch("hogwild", prec)
+            except Exception as exc:
+                raise AssertionError(f"{prec} epoch {t}: {exc}") from exc
             out.append(m.rmse())
         curves[prec] = out
         m.close()
