@@ -26,6 +26,8 @@
  *   - rows that no train entry touches get no regulariser and no gradient (per-entry f_t).
  *   - Alg. 1 with P = 1: every tensor entry updates G with step eta_t.
  *   - eta_t = eta_0 / (1 + mu t) with t the 0-based epoch number.
+ *   - S3CMTF-CP (cp = 1): the core is hyper-diagonal; its off-diagonal entries are not
+ *     parameters, so every core step and the core gradient keep only the diagonal.
  *   - minibatch epoch (not in the paper): all gradients of a batch at the batch-start
  *     parameters; rows take eta * (sum of their gradients) [/ their count in the batch when
  *     row_mean is set]; the core takes eta * core_scale * (mean of its per-entry gradients
@@ -66,6 +68,9 @@ typedef struct {
     double core_scale;           /* minibatch core step multiplier */
     int64_t batch;               /* minibatch size B */
     int row_mean;                /* 0: rows take the batch sum, 1: the batch mean */
+    int cp;                      /* 1: S3CMTF-CP, the core is hyper-diagonal (Section 4.2,
+                                    comparison with SALS): only its diagonal is a parameter,
+                                    so core steps and the core gradient keep the diagonal */
 } s3o_hparams;
 
 /* ------------------------------------------------------------------ small helpers */
@@ -81,6 +86,19 @@ static void odometer_next(int N, const int* J, int* j) {
     for (int n = N - 1; n >= 0; --n) {
         if (++j[n] < J[n]) return;
         j[n] = 0;
+    }
+}
+
+/* S3CMTF-CP: keep only the hyper-diagonal of a core-shaped array (all ranks equal) */
+static void cp_mask(int N, const int* J, const s3o_hparams* hp, double* gG) {
+    if (!hp->cp) return;
+    int j[8] = {0};
+    const int64_t P = core_size(N, J);
+    for (int64_t l = 0; l < P; ++l) {
+        int diag = 1;
+        for (int n = 1; n < N; ++n) diag &= j[n] == j[0];
+        if (!diag) gG[l] = 0.0;
+        odometer_next(N, J, j);
     }
 }
 
@@ -434,6 +452,7 @@ void s3o_full_gradient(const s3o_data* d, const s3o_params* p, const s3o_hparams
         }
         for (int64_t l = 0; l < P; ++l) gG[l] += eG[l];
     }
+    cp_mask(N, J, hp, gG);
     for (int m = 0; m < d->M; ++m) {
         int c = d->cmode[m];
         int Jc = J[c];
@@ -504,6 +523,7 @@ int s3o_epoch_sequential(const s3o_data* d, s3o_params* p, const s3o_hparams* hp
         if (m < 0) {
             compute_gradient(d, p, b, eg, eG);
             add_tensor_reg(d, p, b, cnt, hp->lambda_reg, eg, eG);
+            cp_mask(N, J, hp, eG);
             for (int n = 0; n < N; ++n) {
                 double* u = p->U[n] + (int64_t)d->idx[(int64_t)n * d->nnz + b] * J[n];
                 for (int q = 0; q < J[n]; ++q) u[q] -= eta * eg[n][q];
@@ -585,6 +605,7 @@ int s3o_epoch_minibatch(const s3o_data* d, s3o_params* p, const s3o_hparams* hp,
                     hU[n][i]++;
                     tf[ntouch] = n; tr[ntouch++] = i;
                 }
+                cp_mask(N, J, hp, eG);
                 for (int64_t l = 0; l < P; ++l) DG[l] += eG[l];
                 nt++;
             } else {

@@ -374,3 +374,93 @@ def test_finalize_qr_is_idempotent_and_rejects_rank_deficiency():
     o2 = make(prob, (G, U, V))
     with pytest.raises(ValueError):
         o2.finalize_qr()
+
+
+# ------------------------------------------------------------------ S3CMTF-CP (Section 4.2)
+def _cp_problem(seed=11, J=3):
+    prob, (G, U, V) = random_problem((12, 10, 8), (J, J, J), nnz=40, n_coupled=1, seed=seed,
+                                     coupled_nnz=20)
+    lam = np.random.default_rng(seed).normal(size=J)
+    G = np.zeros((J, J, J))
+    G[np.arange(J), np.arange(J), np.arange(J)] = lam
+    return prob, (G, U, V), lam
+
+
+def test_cp_sequential_epoch_follows_the_cp_formulas():
+    """S3CMTF-CP (hyper-diagonal core, Section 4.2): Algorithm 1 with the CP model written
+    out directly in numpy: x~ = sum_j l_j prod_n a_n[j]; du_n = -e l o prod_{m!=n} a_m +
+    (lambda_reg / c_n) a_n; dl = -e prod_n a_n + (lambda_reg / |Omega|) l; coupled as Eq. (8)."""
+    prob, params, lam = _cp_problem()
+    hp = dict(lr0=0.05, mu=0.0, lambda_reg=0.3, lambda_m=1.5, cp=1)
+    o = make(prob, params, **hp)
+    n_union = prob.train_val.shape[0] + prob.coupled[0].rows.shape[0]
+    order = np.random.default_rng(5).permutation(n_union)
+    o.epoch_sequential(0, order)
+    G1, U1, V1 = o.get_params()
+    # numpy CP reference
+    _, U, V = params
+    U = [u.copy() for u in U]
+    V = [v.copy() for v in V]
+    lam = lam.copy()
+    idx, x = prob.train_idx, prob.train_val
+    nnz = x.shape[0]
+    cnt = [np.bincount(idx[n], minlength=prob.dims[n]) for n in range(3)]
+    c = prob.coupled[0]
+    cntY = np.bincount(c.cols, minlength=c.K)
+    eta, lr, lm = hp["lr0"], hp["lambda_reg"], hp["lambda_m"]
+    for it in order:
+        if it < nnz:
+            a = [U[n][idx[n, it]].copy() for n in range(3)]
+            e = x[it] - np.sum(lam * a[0] * a[1] * a[2])
+            for n in range(3):
+                others = np.prod([a[m] for m in range(3) if m != n], axis=0)
+                U[n][idx[n, it]] -= eta * (-e * lam * others + lr / cnt[n][idx[n, it]] * a[n])
+            lam = lam - eta * (-e * a[0] * a[1] * a[2] + lr / nnz * lam)
+        else:
+            b = it - nnz
+            u, v = U[c.mode][c.rows[b]].copy(), V[0][c.cols[b]].copy()
+            e = c.vals[b] - u @ v
+            U[c.mode][c.rows[b]] -= eta * (-lm * e * v)
+            V[0][c.cols[b]] -= eta * (-lm * e * u + lm * lr / cntY[c.cols[b]] * v)
+    J = lam.shape[0]
+    np.testing.assert_allclose(G1[np.arange(J), np.arange(J), np.arange(J)], lam, rtol=1e-12, atol=1e-14)
+    off = G1.copy()
+    off[np.arange(J), np.arange(J), np.arange(J)] = 0.0
+    assert np.all(off == 0.0)
+    for n in range(3):
+        np.testing.assert_allclose(U1[n], U[n], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(V1[0], V[0], rtol=1e-12, atol=1e-14)
+
+
+def test_cp_full_gradient_is_the_diagonal_of_central_differences():
+    prob, params, lam = _cp_problem(seed=12)
+    o = make(prob, params, lambda_reg=0.2, lambda_m=1.3, cp=1)
+    gG, _, _ = o.full_gradient()
+    G, U, V = params
+    J = lam.shape[0]
+    for j in range(J):
+        Gp, Gm = G.copy(), G.copy()
+        h = 1e-6 * max(1.0, abs(G[j, j, j]))
+        Gp[j, j, j] += h
+        Gm[j, j, j] -= h
+        o.set_params(Gp, U, V)
+        fp = o.loss()[0]
+        o.set_params(Gm, U, V)
+        fm = o.loss()[0]
+        assert gG[j, j, j] == pytest.approx((fp - fm) / (2 * h), rel=1e-6, abs=1e-7)
+    off = gG.copy()
+    off[np.arange(J), np.arange(J), np.arange(J)] = 0.0
+    assert np.all(off == 0.0)
+
+
+def test_cp_minibatch_keeps_the_core_hyperdiagonal():
+    prob, params, lam = _cp_problem(seed=13)
+    o = make(prob, params, lr0=0.02, lambda_reg=0.1, lambda_m=1.0, batch=16, core_scale=2.0, cp=1)
+    n_union = prob.train_val.shape[0] + prob.coupled[0].rows.shape[0]
+    for t in range(3):
+        o.epoch_minibatch(t, np.arange(n_union))
+    G1 = o.get_params()[0]
+    J = lam.shape[0]
+    diag = G1[np.arange(J), np.arange(J), np.arange(J)].copy()
+    G1[np.arange(J), np.arange(J), np.arange(J)] = 0.0
+    assert np.all(G1 == 0.0) and np.all(diag != lam)
