@@ -52,9 +52,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="cfg1")
-    ap.add_argument("--mode", choices=["hogwild", "minibatch", "gradient"], default="hogwild",
+    ap.add_argument("--mode", choices=["hogwild", "minibatch", "gradient", "scalability"],
+                    default="hogwild",
                     help="the step: a HOGWILD or minibatch epoch (nnz-updates/s), or one full "
-                         "gradient pass, the differentiation form (GB/s; e.g. --workload cfg3)")
+                         "gradient pass, the differentiation form (GB/s; e.g. --workload cfg3); "
+                         "scalability: the Section 4.3 sweeps of HOGWILD epoch time over |Omega| "
+                         "and over I")
     ap.add_argument("--cpu-sample", type=int, default=600_000,
                     help="items of the visiting order the CPU oracle baseline processes")
     ap.add_argument("--no-extras", action="store_true",
@@ -332,7 +335,111 @@ def precision_forms(p, order, stream, args, J=16, epochs=4):
     return out
 
 
+def cp_hogwild(p, order, stream, epochs=3):
+    """S3CMTF-CP (hyper-diagonal core) on the same data: HOGWILD epoch time, test RMSE, and
+    the roofline of its O(N J) per-entry kernel, which is bandwidth-shaped: algorithmic DRAM
+    bytes = COO (4N + 4 B) and slot positions (4N B) per tensor entry, COO and positions
+    (20 B) per coupled entry, and each touched row read and written once."""
+    import ctypes as C
+
+    import torch
+
+    from paper_1708_08640_gb300 import _lib as L
+    from paper_1708_08640_gb300.model import S3CMTF
+    G, U, V = synth.init_params(p, 1)
+    J = p.J[0]
+    lam = np.random.default_rng(1).normal(size=J)
+    G = np.zeros(p.J)
+    G[(np.arange(J),) * p.N] = lam
+    m = S3CMTF.from_problem(p, order=order, stream=stream, cp=1)
+    m.set_params(G, U, V)
+    m.set_test(p.test_idx, p.test_val)
+    m.epoch("hogwild")
+    L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 1))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(epochs):
+        m.epoch("hogwild")
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / epochs
+    kms, kn, ke = C.c_double(), C.c_int64(), C.c_int64()
+    L.check(m.lib, m.ctx, m.lib.s3_profile_read(m.ctx, L.S3_K_TENSOR_HOG, C.byref(kms),
+                                                  C.byref(kn), C.byref(ke)))
+    L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 0))
+    rows = sum(int(np.unique(p.train_idx[n]).shape[0]) for n in range(p.N))
+    rows += sum(int(np.unique(c.cols).shape[0]) for c in p.coupled)
+    ld = 4 * ((J + 3) // 4)
+    nbytes = p.nnz * (8 * p.N + 4) + sum(c.nnz * 20 for c in p.coupled) + rows * ld * 4 * 2
+    peaks, src = measured_peaks()
+    k_ms = kms.value / epochs
+    achieved = nbytes / (k_ms / 1000.0) / 1e9
+    out = {"ms_per_epoch": ms, "nnz_updates_per_s": p.n_union / (ms / 1000.0),
+           "test_rmse_after": m.rmse(), "epochs": 1 + epochs, "launch": m.hog_config("fp32"),
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                        "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                        "bytes_per_epoch": nbytes, "kernel_ms_per_epoch": k_ms,
+                        "peak_source": f"{src} hbm_gbs"}}
+    m.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- our arm
+SCAL_NNZ = (100_000, 1_000_000, 10_000_000, 100_000_000)     # at I = 10^4
+SCAL_I = (1_000, 10_000, 100_000, 1_000_000, 10_000_000, 100_000_000)   # at |Omega| = 10^6
+
+
+def run_scalability(args):
+    """Section 4.3 (data scalability): HOGWILD epoch time of the FP32 form on the synthetic
+    I x I x I tensors, over |Omega| at I = 10^4 and over I at |Omega| = 10^6 (coupled
+    I x I matrix with |Omega|/10 entries, J = 10).  The paper's claim: time linear in
+    |Omega|, independent of I.  Parameters from the library's seeded initialisation."""
+    import torch
+
+    from paper_1708_08640_gb300.model import S3CMTF
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+
+    def one(I, nnz):
+        p = synth.make_problem(f"scal:{I}:{nnz}")
+        m = S3CMTF.from_problem(p, order=synth.union_order(p, 2), stream=stream)
+        for _ in range(max(1, args.warmup)):
+            m.epoch("hogwild")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            m.epoch("hogwild")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        m.close()
+        return {"I": I, "nnz": nnz, "train_nnz": p.nnz, "items": p.n_union, "ms_per_epoch": ms,
+                "nnz_updates_per_s": p.n_union / (ms / 1000.0)}
+
+    by_nnz = [one(10_000, n) for n in SCAL_NNZ]
+    by_i = [one(i, 1_000_000) for i in SCAL_I]
+    x = np.array([r["items"] for r in by_nnz], dtype=np.float64)
+    y = np.array([r["ms_per_epoch"] for r in by_nnz])
+    slope, icpt = np.polyfit(x, y, 1)
+    r2 = 1.0 - np.sum((y - (slope * x + icpt)) ** 2) / np.sum((y - y.mean()) ** 2)
+    ti = np.array([r["ms_per_epoch"] for r in by_i])
+    top = by_nnz[-1]
+    line = {"metric": METRIC, "value": top["nnz_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["ms_per_epoch"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "Section 4.3 scalability: I x I x I uniform tensors, coupled "
+                                   "I x I matrix with |Omega|/10 entries, J = 10, FP32 HOGWILD",
+                       "parallelism": "replicas x1"},
+            "scalability": {"over_nnz_at_I_1e4": by_nnz, "over_I_at_nnz_1e6": by_i,
+                            "linear_fit_ms_per_item": slope, "linear_fit_intercept_ms": icpt,
+                            "linear_fit_r2": r2,
+                            "time_ratio_max_over_min_across_I": float(ti.max() / ti.min())}}
+    print(json.dumps(line), flush=True)
+
+
 def run_gradient(args, world, rank, local):
     """The differentiation form: one full-gradient pass (loss gradient with respect to the
     core, every factor and every coupled factor) per step; value = algorithmic GB/s."""
@@ -567,6 +674,8 @@ def run_ours(args, world, rank, local):
             extras["minibatch_epoch"] = {"ms": mb_ms, "nnz_updates_per_s": items / (mb_ms / 1000.0),
                                          "batches": model.info()["n_batches"]}
             m2.close()
+        extras["cp_hogwild"] = cp_hogwild(p, order, stream)
+        extras["forms_j10"] = precision_forms(p, order, stream, args, J=10)
         extras["forms_j16"] = precision_forms(p, order, stream, args, J=16)
         extras["forms_j32"] = precision_forms(p, order, stream, args, J=32, epochs=2)
 
@@ -616,6 +725,9 @@ def main():
         run_reference(args, world, rank)
     elif args.mode == "gradient":
         run_gradient(args, world, rank, local)
+    elif args.mode == "scalability":
+        if rank == 0:
+            run_scalability(args)
     else:
         run_ours(args, world, rank, local)
 

@@ -105,6 +105,10 @@ typedef struct {
                            Fewer CTAs mean fewer stale updates in flight and less throughput. */
     int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = as many as
                            fit); fewer CTAs make its grid-wide barriers cheaper */
+    int cp;             /* 1: S3CMTF-CP (Section 4.2), the core is hyper-diagonal: only G_j..j
+                           are parameters (every mode needs the same rank); core steps and the
+                           core gradient keep the diagonal, s3_set_params zeroes the rest, and
+                           the HOGWILD epoch runs an O(N J) per-entry kernel.  FP32 form. */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.
@@ -145,7 +149,8 @@ int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y, in
  *              tiles moves the core by one group step; not deterministic.
  *   precision  S3_FP32 (CUDA-core FP32), or S3_BF16 (tensor-core contraction with BF16
  *              operands and FP32 accumulation; FP32 master parameters and errors; HOGWILD
- *              mode, 3-way tensors, padded rank 16 or 32, else S3_ERR_ARG).
+ *              mode, 3-way tensors, ranks up to 32, computed at rank 16 or 32 with zero
+ *              padding; else S3_ERR_ARG).
  * Returns S3_ERR_DIVERGED if a non-finite parameter appeared (the parameters are left as
  * they are).  Enqueues work and synchronises once at the end to read the flag. */
 int s3_epoch(s3_ctx* ctx, int mode, int precision);

@@ -57,6 +57,8 @@ struct s3_ctx {
     float* inv_cnt[kMaxF] = {};
     int64_t hog_grid = 1;
     int64_t hog_bf_grid = 0;        // BF16 HOGWILD CTAs (0: the form is not available)
+    int bf_jp = 16;                 // the rank the BF16 form computes at (16 or 32)
+    size_t cp_smem = 0;             // S3CMTF-CP kernel's dynamic shared memory
     size_t hog_bf_smem = 0;
     int64_t hog_tile = 0, hog_per_sm = 0, hog_bf_per_sm = 0, hog_bf_tile = 0, hog_ccap = 0;
     double* qr_parts = nullptr;     // final QR step scratch (allocated at its first call)
@@ -228,6 +230,8 @@ static void fill_params(s3_ctx* ctx) {
     P.M = ctx->M;
     P.ld = ctx->JPR;
     P.ldg = ctx->JPR;
+    P.jp = ctx->JP;
+    P.cp = ctx->hp.cp;
     for (int m = 0; m < ctx->M; ++m) P.cmode[m] = ctx->cmode[m];
     for (int F = 0; F < ctx->N + ctx->M; ++F) P.inv_cnt[F] = ctx->inv_cnt[F];
     P.lambda_reg = ctx->hp.lambda_reg;
@@ -304,9 +308,12 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     ctx->JP = tensor_supported_jp(N, Jmax);
     if (!ctx->JP) return bail(S3_ERR_ARG, "unsupported rank for this order (N=4 supports J<=8)");
     ctx->JPR = round4(ctx->JP);
+    if (hp->cp)
+        for (int n = 1; n < N; ++n)
+            if (J[n] != J[0]) return bail(S3_ERR_ARG, "S3CMTF-CP (hp.cp = 1) needs equal ranks in every mode");
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
-        hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0)
+        hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0 || (hp->cp != 0 && hp->cp != 1))
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];
@@ -400,7 +407,10 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     const int64_t tile_default = N == 3 ? (ctx->JP <= 20 ? 128 : 64) : tile_max;
     const int64_t tile = hp->hog_tile > 0 ? std::min<int64_t>(hp->hog_tile, tile_max) : tile_default;
     ctx->hog_lanes = tensor_hog_lanes(N, ctx->JP, tile);
-    const bool bf16_ok = N == 3 && (ctx->JP == 16 || ctx->JP == 32);
+    // the BF16 form computes at rank 16 or 32 (the tensor cores' granularity), zero-extending
+    // the context's layout
+    const bool bf16_ok = N == 3 && ctx->JP <= 32;
+    ctx->bf_jp = ctx->JP <= 16 ? 16 : 32;
     std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb, kShortSeg);
     if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SLOT, hhog);
     // HOGWILD concurrency of the FP32 form: CTAs resident at once, each on a tile of `tile`
@@ -420,6 +430,18 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(cap, hhog.ngroups));
         ctx->hog_per_sm = per_sm;
         ctx->hog_tile = tile;
+        if (hp->cp) {
+            // S3CMTF-CP runs its own kernel on the same tiles and the same budget of entries in
+            // flight
+            ctx->cp_smem = tensor_cp_smem(ctx->JP, hhog.max_ev, hhog.max_seg, nF);
+            const int cps = ctx->cp_smem <= kMaxSmem
+                                ? std::max(1, tensor_cp_blocks_per_sm(N, ctx->JP, ctx->cp_smem)) : 1;
+            int64_t ccap = (int64_t)cps * ctx->num_sms;
+            if (hp->hog_ctas > 0) ccap = std::min<int64_t>(ccap, hp->hog_ctas);
+            else ccap = std::min<int64_t>(ccap, std::max<int64_t>(1, kHogInflight / tile));
+            ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(ccap, hhog.ngroups));
+            ctx->hog_per_sm = cps;
+        }
     }
     // The BF16 form runs as many CTAs as fit (with hog_ctas as a cap), and its tiles hold as
     // many entries as make the FP32 form's number in flight (at most 128, the MMA's M): both
@@ -431,8 +453,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         const int64_t k = (tensor_hog_bf16_tile() + tile - 1) / tile;
         int64_t ev[kMaxF], sg[kMaxF];
         for (int F = 0; F < nF; ++F) { ev[F] = hhog.max_ev[F] * k; sg[F] = hhog.max_seg[F] * k; }
-        const size_t smem_est = tensor_hog_bf16_smem(ctx->JP, ev, sg, nF);
-        const int per_sm = smem_est <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->JP, smem_est) : 1;
+        const size_t smem_est = tensor_hog_bf16_smem(ctx->bf_jp, ev, sg, nF);
+        const int per_sm = smem_est <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->bf_jp, smem_est) : 1;
         int64_t ctas = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
         if (hp->hog_ctas > 0) ctas = std::min<int64_t>(ctas, hp->hog_ctas);
         const int64_t inflight = ctx->hog_grid * tile;
@@ -514,7 +536,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(cudaMallocHost((void**)&ctx->h_flag, 2 * sizeof(int)));
     CK(tensor_prepare(N, ctx->JP));
     if (bf16_ok) {
-        ctx->hog_bf_smem = tensor_hog_bf16_smem(ctx->JP, ctx->hog_bf.max_ev, ctx->hog_bf.max_seg, nF);
+        ctx->hog_bf_smem = tensor_hog_bf16_smem(ctx->bf_jp, ctx->hog_bf.max_ev, ctx->hog_bf.max_seg, nF);
         ctx->hog_bf_grid = std::min<int64_t>(ctx->hog_bf_grid, ctx->hog_bf.ngroups);
     }
     // staleness-aware step: a row with kappa updates expected in flight at once takes
@@ -550,6 +572,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     }
     // initial parameters
     KL(launch_init_params(ctx->P, ctx->I, ctx->J, ctx->K, ctx->JP, seed, ctx->stream));
+    if (ctx->hp.cp) KL(launch_cp_mask(ctx->P.G, N, ctx->JP, ctx->JPR, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return S3_OK;
 }
@@ -651,6 +674,19 @@ static int enqueue_hogwild(s3_ctx* ctx) {
                                          " bytes of shared memory; lower hog_tile");
     const int row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
     CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
+    if (ctx->hp.cp) {
+        if (ctx->cp_smem > kMaxSmem)
+            return fail(ctx, S3_ERR_ARG, "a CP HOGWILD tile needs " + std::to_string(ctx->cp_smem) +
+                                             " bytes of shared memory; lower hog_tile");
+        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+        KL(launch_tensor_cp_hog(ctx->N, ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter,
+                                (int)ctx->hog_grid, ctx->d_eta, row_mean,
+                                ctx->hp.core_scale / (float)ctx->hog_grid, D.max_ev, D.max_seg,
+                                ctx->stream));
+        CK(prof_mark(ctx, S3_K_TENSOR_HOG));
+        prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
+        return S3_OK;
+    }
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     KL(launch_tensor_hog(ctx->N, ctx->JP, ctx->hog_lanes, ctx->P, D.d, D.ngroups, ctx->d_tile_counter,
                          (int)ctx->hog_grid, ctx->d_eta, row_mean,
@@ -663,9 +699,9 @@ static int enqueue_hogwild(s3_ctx* ctx) {
 
 static int enqueue_hogwild_bf16(s3_ctx* ctx) {
     DevGrouping& D = ctx->hog_bf;
-    if (ctx->N != 3 || (ctx->JP != 16 && ctx->JP != 32))
-        return fail(ctx, S3_ERR_ARG,
-                    "the BF16 form is built for 3-way tensors with ranks 11..16 or 21..32");
+    if (ctx->N != 3 || ctx->JP > 32)
+        return fail(ctx, S3_ERR_ARG, "the BF16 form is built for 3-way tensors with ranks up to 32");
+    if (ctx->hp.cp) return fail(ctx, S3_ERR_ARG, "the BF16 form is built for the Tucker core, not S3CMTF-CP");
     if (ctx->hog_bf_smem > kMaxSmem)
         return fail(ctx, S3_ERR_ARG, "a BF16 HOGWILD tile needs " + std::to_string(ctx->hog_bf_smem) +
                                          " bytes of shared memory (too many coupled entries per tile)");
@@ -675,7 +711,7 @@ static int enqueue_hogwild_bf16(s3_ctx* ctx) {
     const int grid = (int)ctx->hog_bf_grid;
     CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
-    KL(launch_tensor_hog_bf16(ctx->JP, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
+    KL(launch_tensor_hog_bf16(ctx->bf_jp, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
                               ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid, D.max_ev,
                               D.max_seg, ctx->d_kerr, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
@@ -1009,6 +1045,7 @@ extern "C" int s3_get_params(s3_ctx* ctx, float* G, float* const* U, float* cons
 extern "C" int s3_set_params(s3_ctx* ctx, const float* G, const float* const* U, const float* const* V) {
     if (!usable(ctx)) return S3_ERR_STATE;
     if (G) KL(launch_pack_core(ctx->P.G, G, ctx->N, ctx->J, ctx->JP, ctx->stream));
+    if (G && ctx->hp.cp) KL(launch_cp_mask(ctx->P.G, ctx->N, ctx->JP, ctx->JPR, ctx->stream));
     for (int n = 0; n < ctx->N; ++n)
         if (U && U[n]) KL(launch_pack_rows(ctx->P.U[n], ctx->JPR, U[n], ctx->I[n], ctx->J[n], ctx->stream));
     for (int m = 0; m < ctx->M; ++m)

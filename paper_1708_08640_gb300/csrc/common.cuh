@@ -21,6 +21,8 @@ struct DParams {
                                    // factor N+m; 0 for rows without observed entries
     int ld;                        // row stride (floats) of every factor matrix
     int ldg;                       // row stride (floats) of the padded core's last mode
+    int jp;                        // padded rank: the core is jp x .. x jp x ldg
+    int cp;                        // 1: S3CMTF-CP, the core is hyper-diagonal
     int N, M;
     int cmode[kMaxM];
     float lambda_reg, lambda_m, inv_nnz;

@@ -53,8 +53,24 @@ __device__ __forceinline__ void put_slot(float* smem, const HogSmem& H, int F, i
     for (int q = 0; q < JPR / 4; ++q) st4(d + 4 * q, make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]));
 }
 
-// Eq. (8), coupled rows, for the coupled entries of tile t: read the current rows and write
-// the gradients to their slots.  Threads first, first + stride, ... take the entries.
+// A row of P.ld floats (coherent loads) into JP >= P.ld registers, zero beyond: the BF16
+// form computes at a rank padded past the layout's.
+template <int JP>
+__device__ __forceinline__ void load_row_ld(const float* __restrict__ p, int ld, float (&a)[JP]) {
+#pragma unroll
+    for (int q = 0; q < JP / 4; ++q) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * q < ld) v = ld4_cg(p + 4 * q);
+        a[4 * q] = v.x;
+        a[4 * q + 1] = v.y;
+        a[4 * q + 2] = v.z;
+        a[4 * q + 3] = v.w;
+    }
+}
+
+// Eq. (8), coupled rows, for the coupled entries of tile t: read the current rows (P.ld
+// floats each, zero-extended to JP) and write the gradients to their slots (JP floats).
+// Threads first, first + stride, ... take the entries.
 template <int JP>
 __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, int64_t t,
                                             float* smem, const HogSmem& H, int first, int stride) {
@@ -65,9 +81,9 @@ __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, 
         const float lm = P.lambda_m;
         for (int64_t e = c0 + first; e < c1; e += stride) {
             const int32_t r = __ldg(Gr.cr[m] + e), k = __ldg(Gr.cc[m] + e);
-            float u[JP], v[JP];
-            load_row<JP, true>(P.U[c] + (int64_t)r * JPR, u);
-            load_row<JP, true>(P.V[m] + (int64_t)k * JPR, v);
+            float u[JPR], v[JPR];
+            load_row_ld<JPR>(P.U[c] + (int64_t)r * P.ld, P.ld, u);
+            load_row_ld<JPR>(P.V[m] + (int64_t)k * P.ld, P.ld, v);
             float yh = 0.f;
 #pragma unroll
             for (int j = 0; j < JP; ++j) yh = fmaf(u[j], v[j], yh);
@@ -130,19 +146,21 @@ __device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, c
 
 // apply tile t's row steps: per touched row and 4 components, the sum of its slots in slot
 // order, then one vector atomic, step = -eta * (step scale of the row) * (sum or mean of the
-// row's gradients in the tile)
+// row's gradients in the tile).  Slot rows hold JPR floats; global rows P.ld <= JPR, whose
+// P.ld / 4 quads are written.
 template <int JPR>
 __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, const HogSmem& H,
                                           float eta, int row_mean) {
     constexpr int SS = slot_stride(JPR);
     const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
+    const int nq = P.ld / 4;
     for (int F = 0; F < H.nF; ++F) {
         const int nseg = cnts[F];
         const float* sa = smem + H.off[F];
         const int4* tab = reinterpret_cast<const int4*>(smem + H.toff[F]);
         float* base = F < P.N ? P.U[F] : P.V[F - P.N];
-        for (int l = threadIdx.x; l < nseg * (JPR / 4); l += blockDim.x) {
-            const int s = l / (JPR / 4), q = l % (JPR / 4);
+        for (int l = threadIdx.x; l < nseg * nq; l += blockDim.x) {
+            const int s = l / nq, q = l % nq;
             const int4 sg = tab[s];   // row, first slot, events, step scale
             const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
             float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
@@ -154,7 +172,7 @@ __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, c
                 acc.w += v.w;
             }
             const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
-            red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+            red_add_v4(base + (int64_t)rr * P.ld + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
         }
     }
 }

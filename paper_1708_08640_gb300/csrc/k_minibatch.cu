@@ -337,7 +337,16 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
 #pragma unroll
                 for (int o = 1; o < 32; o <<= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
                 const int64_t ntb = t1 - t0;
-                if (lane == 0 && ntb > 0) {
+                bool core_elem = true;   // S3CMTF-CP: only the diagonal is a parameter
+                if (P.cp) {
+                    int64_t r = l;
+                    const int j0 = (int)(r % JP);
+                    for (int n = 1; n < N; ++n) {
+                        r /= JP;
+                        core_elem &= (int)(r % JP) == j0;
+                    }
+                }
+                if (lane == 0 && ntb > 0 && core_elem) {
                     float* g = P.G + (l / JP) * JPR + (l % JP);
                     const float gv = *g;
                     *g = gv + eta * A.core_scale * (sum / (float)ntb) -

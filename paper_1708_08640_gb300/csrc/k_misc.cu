@@ -312,6 +312,16 @@ __global__ void __launch_bounds__(256) k_core(DParams P, int N, int JP, int4 Jv,
                 mul *= Jn[n];
             }
             if (!ok) continue;
+            if (P.cp) {   // S3CMTF-CP: only the diagonal is a parameter
+                int64_t r2 = l;
+                const int j0 = (int)(r2 % JP);
+                bool diag = true;
+                for (int n = 1; n < N; ++n) {
+                    r2 /= JP;
+                    diag &= (int)(r2 % JP) == j0;
+                }
+                if (!diag) continue;
+            }
             Kahan a;
             a.s = out[dst];
             a.c = comp[dst];

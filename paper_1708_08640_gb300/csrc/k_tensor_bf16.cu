@@ -1,4 +1,6 @@
-// BF16 tensor-core form of the S3CMTF tensor pass (3-way, padded rank JP = 16 or 32), sm_103a.
+// BF16 tensor-core form of the S3CMTF tensor pass (3-way, ranks up to 32 computed at JP = 16
+// or 32), sm_103a.  The parameters keep the context's FP32 layout (rows of P.ld floats, the
+// core P.jp x P.jp x P.ldg); the kernel zero-extends them to JP.
 //
 // A CTA of 128 threads takes tiles of 128 tensor entries (the MMA's M), one entry per
 // thread and TMEM lane.  The three dense contractions of the per-entry work run on the
@@ -99,6 +101,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         mbar_init(&s_mbar, 1);
         s_fail = 0;
     }
+    // the BF16 core's padding (past the layout's jp, ldg) is zero for the whole launch
+    for (int l = tid * 16; l < (int)Lt::G_BYTES; l += kBfTile * 16)
+        st_shared_v4(sbase + Lt::OFF_G + l, 0u, 0u, 0u, 0u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -115,16 +120,32 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         int next = 0;
         if (tid == 0) next = atomicAdd(tile_counter, 1);
         hog_tables(Gr, t, smem, H, tid, kBfTile);
-        // ---- the current core as BF16 operand: coalesced float4 reads of G (pair-major),
-        //      each element stored at its place in the (j3, pair) core-matrix layout
-        for (int l = tid * 4; l < Lt::NPAIR * JP; l += kBfTile * 4) {
-            const float4 v = ld4_cg(P.G + l);
-            const int pair = l / JP, j0 = l % JP;
-            const float vv[4] = {v.x, v.y, v.z, v.w};
+        // ---- the current core as BF16 operand: coalesced float4 reads of G (the layout's
+        //      jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix
+        //      layout (pair = j1 JP + j2); the padding past jp stays zero
+        if (P.jp == JP && P.ldg == JP) {
+            // the layout's rank is the kernel's: pair = l / JP with compile-time divisions
+            for (int l = tid * 4; l < Lt::NPAIR * JP; l += kBfTile * 4) {
+                const float4 v = ld4_cg(P.G + l);
+                const int pair = l / JP, j0 = l % JP;
+                const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j0 + i)) =
-                    __float2bfloat16_rn(vv[i]);
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j0 + i)) =
+                        __float2bfloat16_rn(vv[i]);
+            }
+        } else {
+            const int jp = P.jp, ldg = P.ldg;
+            for (int l = tid * 4; l < jp * jp * ldg; l += kBfTile * 4) {
+                const float4 v = ld4_cg(P.G + l);
+                const int j3 = l % ldg, j12 = l / ldg;
+                const int pair = (j12 / jp) * JP + j12 % jp;
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j3 + i)) =
+                        __float2bfloat16_rn(vv[i]);
+            }
         }
         // ---- this thread's entry
         const int64_t e0 = Gr.t_off[t];
@@ -138,9 +159,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             row[0] = __ldg(Gr.tidx[0] + e);
             row[1] = __ldg(Gr.tidx[1] + e);
             row[2] = __ldg(Gr.tidx[2] + e);
-            load_row<JP, true>(P.U[0] + (int64_t)row[0] * JPR, a1);
-            load_row<JP, true>(P.U[1] + (int64_t)row[1] * JPR, a2);
-            load_row<JP, true>(P.U[2] + (int64_t)row[2] * JPR, a3);
+            load_row_ld<JP>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
+            load_row_ld<JP>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
+            load_row_ld<JP>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
             x = __ldg(Gr.tval + e);
         } else {
 #pragma unroll
@@ -255,16 +276,21 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             phase ^= 1;
             tc_fence_after();
             if (nb > 0) {
-                // lane tid holds pair kChunk*c + tid; the regulariser reads the BF16 copy of
-                // G (its term, eta cs lambda / (W |Omega|) G, sits far below G's FP32 ulp)
+                // lane tid holds pair kChunk*c + tid = j1 JP + j2 (inside the layout when
+                // j1, j2 < jp, and then its j3 < ldg go out); the regulariser reads the BF16
+                // copy of G (its term, eta cs lambda / (W |Omega|) G, sits far below G's
+                // FP32 ulp)
                 const int pair = kChunk * c + tid;
-                float* g = P.G + (int64_t)pair * JPR;
+                const int j1 = pair / JP, j2 = pair % JP;
+                const bool inside = j1 < P.jp && j2 < P.jp;
+                float* g = P.G + ((int64_t)j1 * P.jp + j2) * P.ldg;
 #pragma unroll
                 for (int h = 0; h < JP / 16; ++h) {
                     float d[16];
                     tmem_ld16(lane_base + Lt::COL_DG + 16 * h, d);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
+                        if (!inside || 16 * h + 4 * q >= P.ldg) continue;
                         float gv[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i)

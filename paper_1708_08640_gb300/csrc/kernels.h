@@ -170,6 +170,17 @@ cudaError_t launch_tensor_hog_l41(int N, int JP, int L, const DParams& P, const 
                                   const int64_t* max_segs, int64_t ccap, cudaStream_t s);
 int tensor_hog_blocks_l41(int N, int JP, int L, size_t smem);
 
+// S3CMTF-CP (k_cp.cu): the HOGWILD epoch of the hyper-diagonal core model (FP32, one thread
+// per entry, tiles of at most 256 entries; tile bookkeeping as launch_tensor_hog), and the
+// mask that zeroes the padded core's off-diagonal elements.
+size_t tensor_cp_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF);
+int tensor_cp_blocks_per_sm(int N, int JP, size_t smem);
+cudaError_t launch_tensor_cp_hog(int N, int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
+                                 int* tile_counter, int grid, const float* eta, int row_mean,
+                                 float core_step_scale, const int64_t* max_events,
+                                 const int64_t* max_segs, cudaStream_t s);
+cudaError_t launch_cp_mask(float* G, int N, int JP, int ldg, cudaStream_t s);
+
 // Final QR step (k_qr.cu).  launch_qr_factor: CholeskyQR2 of U (rows x J of a row-major
 // matrix with leading dimension ld, J <= 32) into R, Rinv (J x J FP64, upper triangular),
 // with scratch parts ([grid][J * J] FP64), R1 and R1inv (J x J); *bad = 1 if U is

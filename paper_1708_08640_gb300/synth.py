@@ -121,6 +121,8 @@ def unique_coords(rng, n, dims, laws):
         total *= d
     if n > total:
         raise ValueError("more unique coordinates requested than cells")
+    if total >= 1 << 62:
+        return _unique_coords_wide(rng, n, dims, laws)
     # one rank->id permutation per Zipf mode, fixed across redraws
     perms = [rng.permutation(d) if law != "uniform" else None for d, law in zip(dims, laws)]
     keys = np.empty(0, dtype=np.int64)
@@ -135,6 +137,27 @@ def unique_coords(rng, n, dims, laws):
         keys = rng.choice(keys, size=n, replace=False)
     keys = keys[rng.permutation(keys.shape[0])]
     return np.stack(np.unravel_index(keys, dims)).astype(np.int64)
+
+
+def _unique_coords_wide(rng, n, dims, laws):
+    """unique_coords for index spaces beyond 64-bit linear keys: duplicates found by a
+    lexicographic sort of the coordinate columns."""
+    perms = [rng.permutation(d) if law != "uniform" else None for d, law in zip(dims, laws)]
+    cols = np.empty((len(dims), 0), dtype=np.int64)
+    need = n
+    while need > 0:
+        draw = int(need * 1.15) + 64
+        new = np.stack(_draw_coords(rng, draw, dims, laws, perms)).astype(np.int64)
+        cols = np.concatenate([cols, new], axis=1)
+        order = np.lexsort(cols[::-1])
+        srt = cols[:, order]
+        keep = np.ones(srt.shape[1], dtype=bool)
+        keep[1:] = np.any(srt[:, 1:] != srt[:, :-1], axis=0)
+        cols = srt[:, keep]
+        need = n - cols.shape[1]
+    if cols.shape[1] > n:
+        cols = cols[:, rng.choice(cols.shape[1], size=n, replace=False)]
+    return cols[:, rng.permutation(cols.shape[1])]
 
 
 def _planted_values(G, U, idx, chunk=1 << 17):

@@ -63,9 +63,11 @@ def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J, tile, nnz):
     assert_step_close(V[0].cpu().double().numpy(), orc.V[0], V0[0], 1e-5, "V")
 
 
-@pytest.mark.parametrize("J", [16, 24])
+@pytest.mark.parametrize("J", [16, 24, 10, 20])
 def test_bf16_hogwild_single_tile_step(cuda_lib, J):
-    """J = 16: padded rank 16; J = 24: padded rank 32 with zero padding in every operand."""
+    """J = 16: rank 16 as is; J = 24: the layout's rank 32 with zero padding; J = 10 and 20:
+    layouts of rank 10 and 20 (rows of 12 and 20 floats) extended to 16 and 32 inside the
+    kernel."""
     prob, params = one_tile_problem(J)
     (G, U, V), orc = run_one_tile(prob, params, "bf16")
     G0, U0, V0 = params
