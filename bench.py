@@ -58,6 +58,8 @@ def parse():
                          "gradient pass, the differentiation form (GB/s; e.g. --workload cfg3); "
                          "scalability: the Section 4.3 sweeps of HOGWILD epoch time over |Omega| "
                          "and over I")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
+                    help="the step's precision form (bf16: HOGWILD mode, 3-way tensors)")
     ap.add_argument("--cpu-sample", type=int, default=600_000,
                     help="items of the visiting order the CPU oracle baseline processes")
     ap.add_argument("--no-extras", action="store_true",
@@ -586,11 +588,11 @@ def run_ours(args, world, rank, local):
     lib, ctx = model.lib, model.ctx
 
     def step():
-        model.epoch(args.mode, "fp32")
+        model.epoch(args.mode, args.precision)
         return model.rmse()
 
     rmse0 = model.rmse()
-    hog_launch = model.hog_config("fp32") if args.mode == "hogwild" else None
+    hog_launch = model.hog_config(args.precision) if args.mode == "hogwild" else None
     for _ in range(args.warmup):
         step()
     # ---- timed region
@@ -631,14 +633,20 @@ def run_ours(args, world, rank, local):
     flops_per_entry = 6.0 * float(np.prod(J)) if p.N == 3 else (
         6.0 * float(np.prod(J)) + 4.0 * float(np.prod(J[:3])))
     achieved = flops_per_entry * k_entries / (k_ms / 1000.0) / 1e12 if k_ms > 0 else None
-    kname = "k_tensor_hog" if args.mode == "hogwild" else "k_tensor_contrib"
+    kname = "k_tensor_hog" if args.mode == "hogwild" else "k_mb_epoch"
+    if args.precision == "bf16":
+        kname = "k_tensor_hog_bf16"
+        peaks, src = measured_peaks()
+        peak, bound, psrc = peaks["bf16_tflops_sustained"], "tensor", f"{src} bf16_tflops_sustained"
+    else:
+        peak, bound = FP32_PEAK_TFLOPS, "alu"
+        psrc = "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
     traffic = committed_traffic(kname, args.workload)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None,
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "kernel": kname, "launches": k_n,
                 "kernel_ms_per_step": k_ms / args.steps,
-                "flops_per_entry": flops_per_entry,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+                "flops_per_entry": flops_per_entry, "peak_source": psrc}
 
     extras = {}
     if not args.no_extras:
@@ -687,7 +695,7 @@ def run_ours(args, world, rank, local):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         model.update_values(xv, yv)
-        model.epoch(args.mode, "fp32")
+        model.epoch(args.mode, args.precision)
         model.rmse()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
@@ -706,8 +714,9 @@ def run_ours(args, world, rank, local):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32", "data": "synthetic",
-                "config": dict(workload_desc(p, args.mode), parallelism=f"replicas x{world}",
+                "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+                "config": dict(workload_desc(p, args.mode, args.precision),
+                               parallelism=f"replicas x{world}",
                                hogwild_launch=hog_launch),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "updates_by_kind": split,

@@ -292,6 +292,35 @@ def _cfg1_tiny(rng, J=(10, 10, 10)):
     return _rating_like(rng, (2_000, 1_000, 50), 60_000, J, 30_000)
 
 
+def _cfg4(rng, scale=1, J=(20, 20, 20)):
+    """Config 4 (scale): 3-way 10^7 x 10^6 x 1000 with 5*10^8 entries, Zipf(1.1) on modes
+    1-2, uniform mode 3, ratings 1..5 from a planted rank-(20,20,20) Tucker model + noise;
+    coupled: binary symmetric 10^7 x 10^7 on mode 1 (10^8 entries, Zipf(1.1) endpoints),
+    10^6 x 500 on mode 2 (5*10^7 entries ~ U(0,1)), 1000 x 64 dense on mode 3.  `scale`
+    divides modes 1-2, the tensor and the two sparse coupled matrices."""
+    I1, I2, I3 = 10_000_000 // scale, 1_000_000 // scale, 1000
+    nnz = 500_000_000 // scale
+    coords, v, _, _ = _tensor(rng, (I1, I2, I3), nnz, ("zipf1.1", "zipf1.1", "uniform"),
+                              (20, 20, 20), "rating", 0.2)
+    tr_i, tr_v, te_i, te_v = _split(rng, coords, v, 0.10)
+    del coords, v
+    r, c, y = _binary_symmetric(rng, 100_000_000 // scale, I1, "zipf1.1")
+    r2, c2 = _sparse_matrix(rng, 50_000_000 // scale, I2, 500)
+    r3, c3 = np.meshgrid(np.arange(I3, dtype=np.int32), np.arange(64, dtype=np.int32), indexing="ij")
+    cpl = [Coupled(0, I1, r, c, y),
+           Coupled(1, 500, r2, c2, rng.random(r2.shape[0])),
+           Coupled(2, 64, r3.ravel(), c3.ravel(), rng.random(I3 * 64))]
+    hp = dict(lr0=0.001, mu=0.1, lambda_reg=0.1, lambda_m=10.0, batch=4096,
+              core_scale=rating_core_scale(J))
+    rec = (f"3-way {I1}x{I2}x{I3}, {nnz} unique coordinates, modes 1-2 Zipf(1.1), mode 3 "
+           "uniform; planted rank-(20,20,20) core ~ N(0,1), factors ~ U(0,1), standardised to "
+           "mean 3 std 1, + N(0,0.2^2), rounded half-even, clipped to 1..5; 90/10 split; coupled "
+           f"binary symmetric {I1}x{I1} on mode 1 ({100_000_000 // scale} entries, Zipf(1.1) "
+           f"endpoints), {I2}x500 on mode 2 ({50_000_000 // scale} entries ~ U(0,1)), "
+           f"{I3}x64 dense on mode 3")
+    return (I1, I2, I3), J, tr_i, tr_v, te_i, te_v, cpl, hp, rec
+
+
 def _fourway(rng, dims, nnz, nA, nB):
     J = (8, 8, 8, 8)
     coords, v, _, _ = _tensor(rng, dims, nnz, ("zipf1.05",) * 4, J, "real", 0.1)
@@ -344,6 +373,9 @@ PRESETS = {
     "cfg2_small_j32": lambda rng: _cfg1_small(rng, (32, 32, 32)),
     "cfg2_tiny_j16": lambda rng: _cfg1_tiny(rng, (16, 16, 16)),
     "cfg3": _cfg3,
+    "cfg4": _cfg4,
+    "cfg4_small": lambda rng: _cfg4(rng, 10),
+    "cfg4_tiny": lambda rng: _cfg4(rng, 1000),
     "cfg3_small": _cfg3_small,
     "cfg3_tiny": _cfg3_tiny,
 }
