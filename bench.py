@@ -68,6 +68,25 @@ def parse():
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself when
+    the job has one rank.  The process group is NCCL on the GPU box (device "cuda") and can
+    be gloo on the CPU (device "cpu")."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, steps, world, seconds):
+    """Whole-job throughput of a weakly scaled run: every rank processes units_per_rank per
+    step; the job takes the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -483,12 +502,9 @@ def run_gradient(args, world, rank, local):
     clk = clocks.stop()
     barrier()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
-    value = world * gb * args.steps / (ms_total / 1000.0) / 1e9
+    value = job_rate(gb, args.steps, world, ms_total / 1000.0) / 1e9
 
     def read(fam):
         ms, n, e = C.c_double(), C.c_int64(), C.c_int64()
@@ -525,11 +541,8 @@ def run_gradient(args, world, rank, local):
         stream.synchronize()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * gb * args.steps / e2e_s / 1e9, "unit": "GB/s",
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": job_rate(gb, args.steps, world, e2e_s) / 1e9, "unit": "GB/s",
            "h2d_bytes_per_step": 4 * p.n_union, "d2h_bytes_per_step": d2h}
     cpu = None
     if rank == 0 and world == 1:
@@ -609,13 +622,10 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     barrier()
     ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(ms_total, world)
     ms_step = ms_total / args.steps
     items = p.n_union
-    value = world * items * args.steps / (ms_total / 1000.0)
+    value = job_rate(items, args.steps, world, ms_total / 1000.0)
     # the same epochs, counted by kind of update (they run in one kernel)
     split = {"tensor_updates_per_s": world * p.nnz * args.steps / (ms_total / 1000.0),
              "coupled_updates_per_s": world * (p.n_union - p.nnz) * args.steps / (ms_total / 1000.0)}
@@ -699,12 +709,9 @@ def run_ours(args, world, rank, local):
         model.rmse()
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world)
     h2d = 4 * items + 4
-    e2e = {"value": world * items * args.steps / e2e_s, "unit": UNIT,
+    e2e = {"value": job_rate(items, args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12}
 
     cpu = None
