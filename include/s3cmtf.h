@@ -103,8 +103,9 @@ typedef struct {
                            for about 29184 tensor entries in flight in either form, at most as
                            many as fit on the GPU; on 4-way tensors as many as fit).
                            Fewer CTAs mean fewer stale updates in flight and less throughput. */
-    int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = as many as
-                           fit); fewer CTAs make its grid-wide barriers cheaper */
+    int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = one per
+                           SM, at most as many as fit); fewer CTAs make its grid-wide
+                           barriers cheaper, more hide more load latency */
     int cp;             /* 1: S3CMTF-CP (Section 4.2), the core is hyper-diagonal: only G_j..j
                            are parameters (every mode needs the same rank); core steps and the
                            core gradient keep the diagonal, s3_set_params zeroes the rest, and

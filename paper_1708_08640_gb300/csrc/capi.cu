@@ -530,7 +530,10 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(dalloc(ctx, &ctx->d_kerr, 1));
     CK(dalloc(ctx, &ctx->d_bar, 2));
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
-    ctx->mb_grid = std::min<int>(minibatch_epoch_grid(N, ctx->JP, ctx->num_sms), (int)ctx->core_part_n);
+    // one CTA per SM by default: the epoch's grid-wide barriers cost more with every CTA
+    // than a second co-resident CTA gains in latency hiding
+    ctx->mb_grid = std::min<int>({minibatch_epoch_grid(N, ctx->JP, ctx->num_sms), ctx->num_sms,
+                                  (int)ctx->core_part_n});
     if (hp->mb_ctas > 0) ctx->mb_grid = std::min<int>(ctx->mb_grid, hp->mb_ctas);
     CK(cudaMemsetAsync(ctx->d_kerr, 0, sizeof(int), ctx->stream));
     CK(cudaMallocHost((void**)&ctx->h_flag, 2 * sizeof(int)));

@@ -177,52 +177,86 @@ __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, c
     }
 }
 
-// The prefetch warp's part: tile t's metadata into the buffer at meta (see HogMeta).  Only
-// the writing lanes touch the buffer; the CTA barrier that follows publishes it.
-// t >= n_tiles writes only the tile index (the CTA stops there).
+// The prefetch warp's part.  Its lanes hold the ranges of one tile: lane 0 its tensor
+// entries, lanes 1..M its coupled entries of matrix lane - 1, the next nF lanes its segments
+// of factor lane - 1 - M (lo = hi = 0 elsewhere, and for t >= n_tiles).  hog_ranges issues
+// the loads; their values are first used one tile later, so the round trip overlaps the
+// copies of the tile in between.
+__device__ __forceinline__ void hog_ranges(const DParams& P, const DGroup& Gr, int64_t t,
+                                           int64_t n_tiles, const HogSmem& H, int lane,
+                                           int64_t& lo, int64_t& hi) {
+    lo = 0;
+    hi = 0;
+    if (t >= n_tiles) return;
+    if (lane == 0) {
+        lo = Gr.t_off[t];
+        hi = Gr.t_off[t + 1];
+    } else if (lane <= P.M) {
+        lo = Gr.c_off[lane - 1][t];
+        hi = Gr.c_off[lane - 1][t + 1];
+    } else if (lane <= P.M + H.nF) {
+        lo = Gr.seg_off[lane - 1 - P.M][t];
+        hi = Gr.seg_off[lane - 1 - P.M][t + 1];
+    }
+}
+
+// Tile t's metadata into the buffer at meta (see HogMeta), from the ranges of hog_ranges:
+// every array as asynchronous copies, then each segment's row damping (indexed by the
+// segment's row, a second round trip).  Only the copying lanes touch the buffer; the CTA
+// barrier that follows publishes it.  t >= n_tiles writes only the tile index (the CTA
+// stops there).
 template <int N>
 __device__ __forceinline__ void hog_prefetch(const DParams& P, const DGroup& Gr, int64_t t,
-                                             int64_t n_tiles, int* meta, const HogSmem& H,
-                                             int ST, int lane) {
+                                             int64_t n_tiles, int64_t lo, int64_t hi, int* meta,
+                                             const HogSmem& H, int ST, int lane) {
     if (lane == 0) *reinterpret_cast<int64_t*>(meta + kMetaTile) = t;
     if (t >= n_tiles) return;
     const HogMeta& M = H.M;
-    const int64_t e0 = Gr.t_off[t];
-    const int nb = (int)(Gr.t_off[t + 1] - e0);
+    const int cnt = (int)(hi - lo);
+    const int64_t e0 = __shfl_sync(0xffffffffu, lo, 0);
+    const int nb = __shfl_sync(0xffffffffu, cnt, 0);
     for (int l = lane; l < nb; l += 32) {
 #pragma unroll
         for (int n = 0; n < N; ++n) {
-            meta[M.tidx + n * ST + l] = __ldg(Gr.tidx[n] + e0 + l);
-            meta[M.tpos + n * ST + l] = __ldg(Gr.tpos[n] + e0 + l);
+            cp_async4(meta + M.tidx + n * ST + l, Gr.tidx[n] + e0 + l);
+            cp_async4(meta + M.tpos + n * ST + l, Gr.tpos[n] + e0 + l);
         }
-        meta[M.tval + l] = __float_as_int(__ldg(Gr.tval + e0 + l));
+        cp_async4(meta + M.tval + l, Gr.tval + e0 + l);
     }
     int nc = 0;
     for (int m = 0; m < P.M; ++m) {
-        const int64_t c0 = Gr.c_off[m][t];
-        const int n = (int)(Gr.c_off[m][t + 1] - c0);
+        const int64_t c0 = __shfl_sync(0xffffffffu, lo, 1 + m);
+        const int n = __shfl_sync(0xffffffffu, cnt, 1 + m);
         for (int l = lane; l < n; l += 32) {
             const int w = nc + l;
-            meta[M.c_r + w] = __ldg(Gr.cr[m] + c0 + l);
-            meta[M.c_k + w] = __ldg(Gr.cc[m] + c0 + l);
-            meta[M.c_pu + w] = __ldg(Gr.cpos_u[m] + c0 + l);
-            meta[M.c_pv + w] = __ldg(Gr.cpos_v[m] + c0 + l);
-            meta[M.c_y + w] = __float_as_int(__ldg(Gr.cval[m] + c0 + l));
+            cp_async4(meta + M.c_r + w, Gr.cr[m] + c0 + l);
+            cp_async4(meta + M.c_k + w, Gr.cc[m] + c0 + l);
+            cp_async4(meta + M.c_pu + w, Gr.cpos_u[m] + c0 + l);
+            cp_async4(meta + M.c_pv + w, Gr.cpos_v[m] + c0 + l);
+            cp_async4(meta + M.c_y + w, Gr.cval[m] + c0 + l);
             meta[M.c_m + w] = m;
         }
         nc += n;
     }
     for (int F = 0; F < H.nF; ++F) {
-        const int64_t s0 = Gr.seg_off[F][t];
-        const int ns = (int)(Gr.seg_off[F][t + 1] - s0);
+        const int64_t s0 = __shfl_sync(0xffffffffu, lo, 1 + P.M + F);
+        const int ns = __shfl_sync(0xffffffffu, cnt, 1 + P.M + F);
         if (lane == 0) meta[kMetaNseg + F] = ns;
-        int4* tab = reinterpret_cast<int4*>(meta + M.tab[F]);
+        int* tab = meta + M.tab[F];
         for (int l = lane; l < ns; l += 32) {
-            const int32_t row = __ldg(Gr.seg_row[F] + s0 + l);
-            tab[l] = make_int4(row, __ldg(Gr.seg_start[F] + s0 + l), __ldg(Gr.seg_cnt[F] + s0 + l),
-                               __float_as_int(__ldg(Gr.row_damp[F] + row)));
+            cp_async4(tab + 4 * l, Gr.seg_row[F] + s0 + l);
+            cp_async4(tab + 4 * l + 1, Gr.seg_start[F] + s0 + l);
+            cp_async4(tab + 4 * l + 2, Gr.seg_cnt[F] + s0 + l);
         }
     }
+    cp_async_wait_all();
+    // each lane reads back only the rows it copied itself
+    for (int F = 0; F < H.nF; ++F) {
+        const int ns = __shfl_sync(0xffffffffu, cnt, 1 + P.M + F);
+        int* tab = meta + M.tab[F];
+        for (int l = lane; l < ns; l += 32) cp_async4(tab + 4 * l + 3, Gr.row_damp[F] + tab[4 * l]);
+    }
+    cp_async_wait_all();
     if (lane == 0) {
         meta[kMetaNb] = nb;
         meta[kMetaNc] = nc;
@@ -230,31 +264,39 @@ __device__ __forceinline__ void hog_prefetch(const DParams& P, const DGroup& Gr,
 }
 
 // hog_flush over the segment table of a metadata buffer; threads first, first + stride, ...
+// take the (segment, quad) items of all factors in one sequence, so that the long segments
+// at the head of every factor's table land on different threads.
 template <int JPR>
 __device__ __forceinline__ void hog_flush_meta(const DParams& P, const float* smem, const HogSmem& H,
                                                const int* meta, float eta, int row_mean, int first,
                                                int stride) {
-    constexpr int SS = slot_stride(JPR);
-    for (int F = 0; F < H.nF; ++F) {
-        const int nseg = meta[kMetaNseg + F];
+    constexpr int SS = slot_stride(JPR), QD = JPR / 4;
+    int F = 0, fbase = 0, fend = meta[kMetaNseg] * QD;
+    for (int l = first;; l += stride) {
+        while (l >= fend && F < H.nF) {
+            ++F;
+            fbase = fend;
+            if (F < H.nF) fend += meta[kMetaNseg + F] * QD;
+        }
+        if (F >= H.nF) break;
         const float* sa = smem + H.off[F];
         const int4* tab = reinterpret_cast<const int4*>(meta + H.M.tab[F]);
         float* base = F < P.N ? P.U[F] : P.V[F - P.N];
-        for (int l = first; l < nseg * (JPR / 4); l += stride) {
-            const int s = l / (JPR / 4), q = l % (JPR / 4);
-            const int4 sg = tab[s];   // row, first slot, events, step scale
-            const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
-            float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
-            for (int k = 1; k < cnt; ++k) {
-                const float4 v = *reinterpret_cast<const float4*>(sa + (st + k) * SS + 4 * q);
-                acc.x += v.x;
-                acc.y += v.y;
-                acc.z += v.z;
-                acc.w += v.w;
-            }
-            const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
-            red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+        const int s = (l - fbase) / QD, q = (l - fbase) % QD;
+        const int4 sg = tab[s];   // row, first slot, events, step scale
+        const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
+        const float* src = sa + st * SS + 4 * q;
+        float4 acc = *reinterpret_cast<const float4*>(src);
+#pragma unroll 4
+        for (int k = 1; k < cnt; ++k) {
+            const float4 v = *reinterpret_cast<const float4*>(src + k * SS);
+            acc.x += v.x;
+            acc.y += v.y;
+            acc.z += v.z;
+            acc.w += v.w;
         }
+        const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
+        red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
     }
 }
 

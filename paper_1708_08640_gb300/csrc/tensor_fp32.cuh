@@ -343,6 +343,7 @@ struct CoreTile {
             float tile[JP];
 #pragma unroll
             for (int j = 0; j < JP; ++j) tile[j] = 0.f;
+#pragma unroll 4
             for (int b = slice; b < nb; b += KS) {
                 float w = stage[(0 * ST + b) * JPR + jj[0]];
 #pragma unroll

@@ -20,10 +20,13 @@ namespace s3 {
 // and x~ are added with shuffles), so a tile holds kTile / L entries: fewer entries in flight
 // (less staleness) for the same number of threads.
 // A CTA has kTile compute threads and one prefetch warp.  While the compute threads work on
-// a tile, the prefetch warp claims the next tile and loads everything it will read besides
-// the parameters (indices, values, slot positions, coupled entries, segment table) into the
-// other metadata buffer, so that a tile's critical path starts at its row gathers; the core
-// is re-read at the start of every tile, while those gathers are in flight.
+// a tile, the prefetch warp loads everything the next tile will read besides the parameters
+// (indices, values, slot positions, coupled entries, segment table) into the other metadata
+// buffer, so that a tile's critical path starts at its row gathers; the core is re-read at
+// the start of every tile, while those gathers are in flight.  The prefetch warp runs its
+// own three-stage pipeline: it claims a tile three tiles ahead, reads the array ranges of
+// the tile two ahead and copies the tile one ahead, so that only the copies' round trips
+// fall into a tile.
 constexpr int kHogThreads = kTile + 32;
 
 template <int N, int JP>
@@ -34,6 +37,10 @@ struct HogCore {
 
 __device__ __forceinline__ void compute_barrier() {
     asm volatile("bar.sync 1, %0;" :: "r"(kTile) : "memory");
+}
+// the end of a tile, for the compute threads and the prefetch warp (which run separate loops)
+__device__ __forceinline__ void tile_barrier() {
+    asm volatile("bar.sync 2, %0;" :: "r"(kHogThreads) : "memory");
 }
 
 // two CTAs per SM for padded ranks up to 16 (at most 112 registers a thread), one above
@@ -59,26 +66,45 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
     const bool pf = tid >= kTile;          // the prefetch warp
     const int lane = tid & 31;
     const int slot = tid / L, lsub = tid % L;
+    (void)slot;
+    (void)lsub;
     int* meta_base = reinterpret_cast<int*>(smem);
-    // the first tile
     if (pf) {
-        int t0 = 0;
-        if (lane == 0) t0 = atomicAdd(tile_counter, 1);
-        t0 = __shfl_sync(0xffffffffu, t0, 0);
-        hog_prefetch<N>(P, Gr, t0, n_tiles, meta_base + H.meta[0], H, ST, lane);
+        // the prefetch pipeline: the tile in the buffer being computed, the tile to copy next,
+        // the tile after it (its ranges in flight) and the claim after that
+        int c0 = 0, c1 = 0, claim = 0;
+        if (lane == 0) {
+            c0 = atomicAdd(tile_counter, 1);
+            c1 = atomicAdd(tile_counter, 1);
+            claim = atomicAdd(tile_counter, 1);
+        }
+        int64_t t_cur = __shfl_sync(0xffffffffu, c0, 0);
+        int64_t t_after = __shfl_sync(0xffffffffu, c1, 0);
+        int64_t lo, hi, lo_after, hi_after;
+        hog_ranges(P, Gr, t_cur, n_tiles, H, lane, lo, hi);
+        hog_ranges(P, Gr, t_after, n_tiles, H, lane, lo_after, hi_after);
+        hog_prefetch<N>(P, Gr, t_cur, n_tiles, lo, hi, meta_base + H.meta[0], H, ST, lane);
+        tile_barrier();
+        for (int it = 0; t_cur < n_tiles; ++it) {
+            const int64_t t_next = t_after;
+            lo = lo_after;
+            hi = hi_after;
+            t_after = __shfl_sync(0xffffffffu, claim, 0);
+            if (lane == 0) claim = atomicAdd(tile_counter, 1);
+            hog_ranges(P, Gr, t_after, n_tiles, H, lane, lo_after, hi_after);
+            hog_prefetch<N>(P, Gr, t_next, n_tiles, lo, hi, meta_base + H.meta[(it & 1) ^ 1], H, ST, lane);
+            tile_barrier();
+            t_cur = t_next;
+        }
+        return;
     }
-    __syncthreads();
+    tile_barrier();
     for (int it = 0;; ++it) {
         const int b = it & 1;
         const int* mb = meta_base + H.meta[b];
         const int64_t t = *reinterpret_cast<const int64_t*>(mb + kMetaTile);
         if (t >= n_tiles) break;
-        if (pf) {
-            int nx = 0;
-            if (lane == 0) nx = atomicAdd(tile_counter, 1);
-            nx = __shfl_sync(0xffffffffu, nx, 0);
-            hog_prefetch<N>(P, Gr, nx, n_tiles, meta_base + H.meta[b ^ 1], H, ST, lane);
-        } else {
+        {
             // the current core (coherent: other CTAs add to it), once the tile's row gathers
             // are in flight
             auto reload_core = [&]() {
@@ -224,7 +250,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             }
             hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kTile);
         }
-        __syncthreads();
+        tile_barrier();
     }
 }
 
