@@ -398,13 +398,19 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     }
     HostGrouping hmb, hhog, hgrad, hhog_bf;
     const int nF = N + n_coupled;
-    // FP32 HOGWILD tiles hold at most 128 entries for 3-way tensors (two lanes per entry;
-    // tiles of up to 64 entries take four), 256 for 4-way (one lane).  Default for 3-way
-    // tensors: tiles of 128 entries (64 for ranks above 20, whose core fills most of shared
-    // memory) and about kHogInflight entries in flight (CTAs capped at kHogInflight / tile):
-    // the HOGWILD test-RMSE curve then stays within 1% of Algorithm 1's on the cfg1 workload.
-    const int64_t tile_max = N == 3 ? kTile / 2 : kTile;
-    const int64_t tile_default = N == 3 ? (ctx->JP <= 20 ? 128 : 64) : tile_max;
+    // FP32 HOGWILD tiles hold at most T / 2 entries for 3-way tensors (T compute threads,
+    // two lanes per entry; tiles of up to T / 4 entries take four), T for 4-way (one lane),
+    // T = hog_compute_threads.  Default for 3-way tensors: the largest tile (192 entries up
+    // to padded rank 16, 128 at 20, 64 at 32, whose core fills most of shared memory) and
+    // about kHogInflight entries in flight (CTAs capped at kHogInflight / tile): the HOGWILD
+    // test-RMSE curve then stays within 1% of Algorithm 1's on the cfg1 workload.
+    const int64_t hog_t = hog_compute_threads(N, ctx->JP);
+    const int64_t tile_max = N == 3 ? hog_t / 2 : hog_t;
+    // (S3CMTF-CP runs its own one-thread-per-entry kernel on these tiles: 128 entries on 228
+    // CTAs, the same budget in flight)
+    const int64_t tile_default = N != 3 ? tile_max
+                                 : hp->cp ? std::min<int64_t>(128, tile_max)
+                                 : (ctx->JP <= 20 ? tile_max : hog_t / 4);
     const int64_t tile = hp->hog_tile > 0 ? std::min<int64_t>(hp->hog_tile, tile_max) : tile_default;
     ctx->hog_lanes = tensor_hog_lanes(N, ctx->JP, tile);
     // the BF16 form computes at rank 16 or 32 (the tensor cores' granularity), zero-extending
@@ -446,24 +452,34 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // The BF16 form runs as many CTAs as fit (with hog_ctas as a cap), and its tiles hold as
     // many entries as make the FP32 form's number in flight (at most 128, the MMA's M): both
     // forms then take the same lock-free schedule, and differ by their arithmetic only.  Its
-    // shared memory is bounded before its grouping exists from the FP32 grouping's largest
-    // tile, ceil(128 / tile) times over.
+    // grouping is built for two CTAs per SM first, and again for one when that grouping's
+    // shared memory does not let two fit.
     int64_t bf_tile = tensor_hog_bf16_tile();
     if (msg.empty() && bf16_ok) {
-        const int64_t k = (tensor_hog_bf16_tile() + tile - 1) / tile;
-        int64_t ev[kMaxF], sg[kMaxF];
-        for (int F = 0; F < nF; ++F) { ev[F] = hhog.max_ev[F] * k; sg[F] = hhog.max_seg[F] * k; }
-        const size_t smem_est = tensor_hog_bf16_smem(ctx->bf_jp, ev, sg, nF);
-        const int per_sm = smem_est <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->bf_jp, smem_est) : 1;
-        int64_t ctas = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
-        if (hp->hog_ctas > 0) ctas = std::min<int64_t>(ctas, hp->hog_ctas);
         const int64_t inflight = ctx->hog_grid * tile;
-        bf_tile = std::max<int64_t>(16, std::min<int64_t>(tensor_hog_bf16_tile(),
-                                                          inflight / std::max<int64_t>(ctas, 1)));
-        ctx->hog_bf_grid = ctas;
-        ctx->hog_bf_per_sm = per_sm;
-        ctx->hog_bf_tile = bf_tile;
-        msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, bf_tile, POS_SLOT, hhog_bf);
+        auto ctas_for = [&](int want) {
+            int64_t c = (int64_t)want * ctx->num_sms;
+            return hp->hog_ctas > 0 ? std::min<int64_t>(c, hp->hog_ctas) : c;
+        };
+        auto tile_for = [&](int64_t ctas) {
+            return std::max<int64_t>(16, std::min<int64_t>(tensor_hog_bf16_tile(),
+                                                           inflight / std::max<int64_t>(ctas, 1)));
+        };
+        for (int want = 2; want >= 1; --want) {
+            const int64_t ctas = ctas_for(want);
+            bf_tile = tile_for(ctas);
+            hhog_bf = HostGrouping{};
+            msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, bf_tile, POS_SLOT, hhog_bf);
+            if (!msg.empty()) break;
+            const size_t smem = tensor_hog_bf16_smem(ctx->bf_jp, hhog_bf.max_ev, hhog_bf.max_seg, nF);
+            const int per_sm = smem <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->bf_jp, smem) : 0;
+            if (per_sm >= want || want == 1 || tile_for(ctas_for(want - 1)) == bf_tile) {
+                ctx->hog_bf_grid = per_sm >= want ? ctas : ctas_for(std::max(per_sm, 1));
+                ctx->hog_bf_per_sm = std::max(per_sm, 1);
+                ctx->hog_bf_tile = bf_tile;
+                break;
+            }
+        }
     }
     const int64_t grad_chunk = 1 << 20;
     if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad, kShortSeg,

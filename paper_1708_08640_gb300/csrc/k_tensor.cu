@@ -134,9 +134,8 @@ __global__ void __launch_bounds__(kTile) k_tensor_fwd(DParams P, IdxPtrs idx, co
     X(3, 2) X(3, 4) X(3, 5) X(3, 8) X(3, 10) X(3, 16) X(3, 20) X(3, 32) X(4, 2) X(4, 4) X(4, 8)
 
 int tensor_hog_lanes(int N, int JP, int64_t tile) {
-    (void)JP;
     if (N != 3) return 1;
-    return tile <= kTile / 4 ? 4 : 2;
+    return tile <= hog_compute_threads(N, JP) / 4 ? 4 : 2;
 }
 
 int tensor_supported_jp(int N, int J) {

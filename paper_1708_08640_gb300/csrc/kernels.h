@@ -75,8 +75,15 @@ cudaError_t launch_tensor_fwd(int N, int JP, const DParams& P, const int32_t* co
                               cudaStream_t s);
 
 int tensor_supported_jp(int N, int J);   // smallest instantiated JP >= J, or 0
+// Compute threads of a CTA of the FP32 HOGWILD kernel (it adds one prefetch warp): 384
+// for 3-way tensors up to padded rank 16 (one CTA per SM, tiles of up to 192 entries on
+// two lanes), else 256.  A tile's phases are latency-bound; larger tiles on fewer CTAs
+// hold the same number of entries in flight with fewer tile latencies per entry.
+__host__ __device__ constexpr int hog_compute_threads(int N, int JP) {
+    return N == 3 && JP <= 16 ? 384 : 256;
+}
 // lanes per entry of the FP32 HOGWILD kernel for tiles of `tile` entries (tiles hold at
-// most kTile / lanes entries)
+// most hog_compute_threads / lanes entries)
 int tensor_hog_lanes(int N, int JP, int64_t tile);
 // sets the dynamic shared-memory limits of this shape's gradient and forward kernels
 cudaError_t tensor_prepare(int N, int JP);

@@ -318,50 +318,106 @@ struct CoreAcc {
 // One tile's core step added lock-free to the core in global memory: thread (q, slice) sums
 // its slice of the tile's entries for multi-index q and all JP values of the last mode, then
 // adds  sc * sum - rg * G  (rg only once, by slice 0) with atomics.
-template <int N, int JP, int ST = kTile>
+template <int N, int JP, int ST = kTile, int T = kTile>
 struct CoreTile {
     static constexpr int JPR = round4(JP);
     static constexpr int Q = ipow_t<JP, N - 1>::v;
-    static constexpr int KS = (kTile / Q) > 0 ? (kTile / Q) : 1;
-    static constexpr int QPT = (Q + kTile - 1) / kTile;
+    static constexpr int KS = (T / Q) > 0 ? (T / Q) : 1;
+    static constexpr int QPT = (Q + T - 1) / T;
+    // entries per step of the accumulation loop: their shared-memory loads are independent of
+    // the accumulation chain, which keeps the entries' order
+    static constexpr int U = JP <= 16 ? 4 : (JP <= 20 ? 2 : 1);
+    // with several slices, slices 1.. hand their sums to slice 0 through the stage (read by
+    // then), so that one atomic per element reaches the core instead of KS
+    static constexpr bool kReduce = KS > 1 && (KS - 1) * Q * JPR <= N * ST * JPR;
 
-    __device__ __forceinline__ static void apply(const float* __restrict__ stage, int nb,
-                                                 const float* __restrict__ sG, float* G,
-                                                 float sc, float rg) {
+    // thread (q, slice)'s sum over its slice of the tile's entries
+    __device__ __forceinline__ static void accumulate(const float* __restrict__ stage, int nb, int q,
+                                                      int slice, float (&tile)[JP]) {
+        int jj[N - 1];
+        {
+            int r = q;
+#pragma unroll
+            for (int n = N - 2; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
+        }
+#pragma unroll
+        for (int j = 0; j < JP; ++j) tile[j] = 0.f;
+        int b = slice;
+        for (; b + (U - 1) * KS < nb; b += U * KS) {
+            float w[U], r[U][JP];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int bu = b + u * KS;
+                w[u] = stage[(0 * ST + bu) * JPR + jj[0]];
+#pragma unroll
+                for (int n = 1; n < N - 1; ++n) w[u] *= stage[(n * ST + bu) * JPR + jj[n]];
+                load_grow<JP>(stage + ((N - 1) * ST + bu) * JPR, r[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int j = 0; j < JP; ++j) tile[j] = fmaf(w[u], r[u][j], tile[j]);
+        }
+        for (; b < nb; b += KS) {
+            float w = stage[(0 * ST + b) * JPR + jj[0]];
+#pragma unroll
+            for (int n = 1; n < N - 1; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
+            float r[JP];
+            load_grow<JP>(stage + ((N - 1) * ST + b) * JPR, r);
+#pragma unroll
+            for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
+        }
+    }
+
+    // G[q] += sc * tile - rg * G[q] (rg only when add_reg)
+    __device__ __forceinline__ static void add(float* G, const float* __restrict__ sG, int q,
+                                               const float (&tile)[JP], float sc, float rg,
+                                               bool add_reg) {
+        float g[JP];
+        load_grow<JP>(sG + q * JPR, g);
+        float d[JPR];
+#pragma unroll
+        for (int j = 0; j < JPR; ++j) d[j] = j < JP ? fmaf(sc, tile[j], add_reg ? -rg * g[j] : 0.f) : 0.f;
+#pragma unroll
+        for (int c = 0; c < JPR / 4; ++c)
+            red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+    }
+
+    // Every one of the T threads calls apply (it has CTA barriers over T threads when
+    // kReduce; the stage is overwritten then).
+    __device__ __forceinline__ static void apply(float* stage, int nb, const float* __restrict__ sG,
+                                                 float* G, float sc, float rg) {
         const int t = threadIdx.x;
         const int slice = KS > 1 ? t / Q : 0;
-#pragma unroll
-        for (int k = 0; k < QPT; ++k) {
-            const int q = KS > 1 ? (t % Q) : (t + k * kTile);
-            if (slice >= KS || q >= Q) continue;
-            int jj[N - 1];
-            {
-                int r = q;
-#pragma unroll
-                for (int n = N - 2; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
-            }
+        if constexpr (kReduce) {
+            const int q = t % Q;
+            const bool act = slice < KS;
             float tile[JP];
+            if (act) accumulate(stage, nb, q, slice, tile);
+            asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
+            if (act && slice > 0) {
+                float* o = stage + ((slice - 1) * Q + q) * JPR;
 #pragma unroll
-            for (int j = 0; j < JP; ++j) tile[j] = 0.f;
-#pragma unroll 4
-            for (int b = slice; b < nb; b += KS) {
-                float w = stage[(0 * ST + b) * JPR + jj[0]];
-#pragma unroll
-                for (int n = 1; n < N - 1; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
-                float r[JP];
-                load_grow<JP>(stage + ((N - 1) * ST + b) * JPR, r);
-#pragma unroll
-                for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
+                for (int j = 0; j < JP; ++j) o[j] = tile[j];
             }
-            float g[JP];
-            load_grow<JP>(sG + q * JPR, g);
-            float d[JPR];
+            asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
+            if (act && slice == 0) {
+                for (int sl = 1; sl < KS; ++sl) {
+                    const float* o = stage + ((sl - 1) * Q + q) * JPR;
 #pragma unroll
-            for (int j = 0; j < JPR; ++j)
-                d[j] = j < JP ? fmaf(sc, tile[j], slice == 0 ? -rg * g[j] : 0.f) : 0.f;
+                    for (int j = 0; j < JP; ++j) tile[j] += o[j];
+                }
+                add(G, sG, q, tile, sc, rg, true);
+            }
+        } else {
 #pragma unroll
-            for (int c = 0; c < JPR / 4; ++c)
-                red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+            for (int k = 0; k < QPT; ++k) {
+                const int q = KS > 1 ? (t % Q) : (t + k * T);
+                if (slice >= KS || q >= Q) continue;
+                float tile[JP];
+                accumulate(stage, nb, q, slice, tile);
+                add(G, sG, q, tile, sc, rg, slice == 0);
+            }
         }
     }
 };

@@ -17,9 +17,10 @@ namespace s3 {
 // and adds the row steps with vector atomics, and adds its share of the core step to G
 // (lock-free, like the rows).
 // L adjacent lanes share an entry (3-way: the j1 range is split, the lanes' parts of p2, p3
-// and x~ are added with shuffles), so a tile holds kTile / L entries: fewer entries in flight
+// and x~ are added with shuffles), so a tile holds T / L entries: fewer entries in flight
 // (less staleness) for the same number of threads.
-// A CTA has kTile compute threads and one prefetch warp.  While the compute threads work on
+// A CTA has T = hog_compute_threads(N, JP) compute threads and one prefetch warp.  While the
+// compute threads work on
 // a tile, the prefetch warp loads everything the next tile will read besides the parameters
 // (indices, values, slot positions, coupled entries, segment table) into the other metadata
 // buffer, so that a tile's critical path starts at its row gathers; the core is re-read at
@@ -27,7 +28,8 @@ namespace s3 {
 // own three-stage pipeline: it claims a tile three tiles ahead, reads the array ranges of
 // the tile two ahead and copies the tile one ahead, so that only the copies' round trips
 // fall into a tile.
-constexpr int kHogThreads = kTile + 32;
+// threads of a CTA: T = hog_compute_threads(N, JP) compute threads and the prefetch warp
+__host__ __device__ constexpr int hog_threads(int N, int JP) { return hog_compute_threads(N, JP) + 32; }
 
 template <int N, int JP>
 struct HogCore {
@@ -35,17 +37,19 @@ struct HogCore {
     static constexpr int floats = Q * round4(JP);
 };
 
+template <int T>
 __device__ __forceinline__ void compute_barrier() {
-    asm volatile("bar.sync 1, %0;" :: "r"(kTile) : "memory");
+    asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
 }
 // the end of a tile, for the compute threads and the prefetch warp (which run separate loops)
+template <int T>
 __device__ __forceinline__ void tile_barrier() {
-    asm volatile("bar.sync 2, %0;" :: "r"(kHogThreads) : "memory");
+    asm volatile("bar.sync 2, %0;" :: "r"(T + 32) : "memory");
 }
 
-// two CTAs per SM for padded ranks up to 16 (at most 112 registers a thread), one above
+// one CTA per SM (two for 4-way tensors up to padded rank 8: at most 112 registers a thread)
 template <int N, int JP, int L>
-__global__ void __launch_bounds__(kHogThreads, (JP <= 16 ? 2 : 1))
+__global__ void __launch_bounds__(hog_threads(N, JP), (N == 4 ? 2 : 1))
 k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                                                             int* tile_counter, const float* eta_p,
                                                             int row_mean, float core_step_scale,
@@ -53,7 +57,8 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
     static_assert(L == 1 || N == 3, "lanes per entry > 1 is built for 3-way tensors");
     constexpr int JPR = round4(JP);
     constexpr int JH = (JP + L - 1) / L;
-    constexpr int ST = kTile / L;          // entries per tile at most: rows per stage block
+    constexpr int kT = hog_compute_threads(N, JP);   // compute threads
+    constexpr int ST = kT / L;             // entries per tile at most: rows per stage block
     constexpr int GF = HogCore<N, JP>::floats;
     // coupled rows of the first round are gathered together with the tensor rows when they
     // fit in the registers
@@ -63,7 +68,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
     float* stage = smem + GF;
     const float eta = *eta_p;
     const int tid = threadIdx.x;
-    const bool pf = tid >= kTile;          // the prefetch warp
+    const bool pf = tid >= kT;             // the prefetch warp
     const int lane = tid & 31;
     const int slot = tid / L, lsub = tid % L;
     (void)slot;
@@ -84,7 +89,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
         hog_ranges(P, Gr, t_cur, n_tiles, H, lane, lo, hi);
         hog_ranges(P, Gr, t_after, n_tiles, H, lane, lo_after, hi_after);
         hog_prefetch<N>(P, Gr, t_cur, n_tiles, lo, hi, meta_base + H.meta[0], H, ST, lane);
-        tile_barrier();
+        tile_barrier<kT>();
         for (int it = 0; t_cur < n_tiles; ++it) {
             const int64_t t_next = t_after;
             lo = lo_after;
@@ -93,12 +98,12 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             if (lane == 0) claim = atomicAdd(tile_counter, 1);
             hog_ranges(P, Gr, t_after, n_tiles, H, lane, lo_after, hi_after);
             hog_prefetch<N>(P, Gr, t_next, n_tiles, lo, hi, meta_base + H.meta[(it & 1) ^ 1], H, ST, lane);
-            tile_barrier();
+            tile_barrier<kT>();
             t_cur = t_next;
         }
         return;
     }
-    tile_barrier();
+    tile_barrier<kT>();
     for (int it = 0;; ++it) {
         const int b = it & 1;
         const int* mb = meta_base + H.meta[b];
@@ -108,8 +113,8 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             // the current core (coherent: other CTAs add to it), once the tile's row gathers
             // are in flight
             auto reload_core = [&]() {
-                for (int l = tid * 4; l < GF; l += kTile * 4) st4(sG + l, ld4_cg(P.G + l));
-                compute_barrier();
+                for (int l = tid * 4; l < GF; l += kT * 4) st4(sG + l, ld4_cg(P.G + l));
+                compute_barrier<kT>();
             };
             const int nb = mb[kMetaNb];
             const int nc = mb[kMetaNc];
@@ -232,7 +237,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                 if (hc) hog_coupled_one<JP>(P, smem, H, cm, ck, mb[M.c_pu + tid], mb[M.c_pv + tid],
                                             __int_as_float(mb[M.c_y + tid]), cu, cv);
             }
-            for (int e = kEarlyCpl ? tid + kTile : tid; e < nc; e += kTile) {
+            for (int e = kEarlyCpl ? tid + kT : tid; e < nc; e += kT) {
                 float u[JP], v[JP];
                 const int m = mb[M.c_m + e], k = mb[M.c_k + e];
                 load_row<JP, true>(P.U[P.cmode[m]] + (int64_t)mb[M.c_r + e] * JPR, u);
@@ -240,17 +245,17 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                 hog_coupled_one<JP>(P, smem, H, m, k, mb[M.c_pu + e], mb[M.c_pv + e],
                                     __int_as_float(mb[M.c_y + e]), u, v);
             }
-            compute_barrier();
+            compute_barrier<kT>();
             // core: this tile's share of the core step,
             //   G += eta * cs / W * (sum_b e_b a1 o..o aN / n_t - lambda_reg / |Omega| * G)
             if (nb > 0) {
                 const float sc = eta * core_step_scale / (float)nb;
                 const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
-                CoreTile<N, JP, ST>::apply(stage, nb, sG, P.G, sc, rg);
+                CoreTile<N, JP, ST, kT>::apply(stage, nb, sG, P.G, sc, rg);
             }
-            hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kTile);
+            hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kT);
         }
-        tile_barrier();
+        tile_barrier<kT>();
     }
 }
 
@@ -260,16 +265,16 @@ static inline size_t hog_core_floats(int N, int JP) {
     return q * round4(JP);
 }
 
-// the HOGWILD kernel's fixed shared memory (floats): the core and a stage of kTile / L rows
+// the HOGWILD kernel's fixed shared memory (floats): the core and a stage of T / L rows
 // per mode
 static inline size_t hog_fixed_floats(int N, int JP, int L) {
-    return hog_core_floats(N, JP) + (size_t)N * (kTile / L) * round4(JP);
+    return hog_core_floats(N, JP) + (size_t)N * (hog_compute_threads(N, JP) / L) * round4(JP);
 }
 
 // the whole layout: core, stage, slots, metadata buffers
 static inline size_t hog_layout(int N, int JP, int L, const int64_t* max_events,
                                 const int64_t* max_segs, int64_t ccap, int nF, HogSmem* H) {
-    return hog_meta_smem_floats(round4(JP), N, kTile / L, max_events, max_segs, ccap, nF, H,
+    return hog_meta_smem_floats(round4(JP), N, hog_compute_threads(N, JP) / L, max_events, max_segs, ccap, nF, H,
                                 hog_fixed_floats(N, JP, L));
 }
 
@@ -296,7 +301,7 @@ static inline size_t hog_layout(int N, int JP, int L, const int64_t* max_events,
     if (N == NN && JP == JJ && L == LL) {                                                      \
         cudaError_t e = prep(k_tensor_hog<NN, JJ, LL>, smem);                                  \
         if (e != cudaSuccess) return e;                                                        \
-        k_tensor_hog<NN, JJ, LL><<<grid, kHogThreads, smem, s>>>(P, G, n_tiles, tile_counter, eta, \
+        k_tensor_hog<NN, JJ, LL><<<grid, hog_threads(NN, JJ), smem, s>>>(P, G, n_tiles, tile_counter, eta, \
                                                            row_mean, core_step_scale, H);      \
         return cudaGetLastError();                                                             \
     }
@@ -304,7 +309,7 @@ static inline size_t hog_layout(int N, int JP, int L, const int64_t* max_events,
 #define S3_HOG_BLOCKS_ONE(NN, JJ, LL)                                                          \
     if (N == NN && JP == JJ && L == LL) {                                                      \
         if (prep(k_tensor_hog<NN, JJ, LL>, smem) != cudaSuccess) return 0;                     \
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tensor_hog<NN, JJ, LL>, kHogThreads, \
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_tensor_hog<NN, JJ, LL>, hog_threads(NN, JJ), \
                                                           smem) != cudaSuccess)                \
             return 0;                                                                          \
         return nb;                                                                             \
