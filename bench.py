@@ -42,7 +42,8 @@ KERNEL_SOURCES = ["paper_1708_08640_gb300/csrc/tensor_hog.cuh",
                   "paper_1708_08640_gb300/csrc/k_tensor_hog2.cu",
                   "paper_1708_08640_gb300/csrc/hog_common.cuh",
                   "paper_1708_08640_gb300/csrc/tensor_fp32.cuh",
-                  "paper_1708_08640_gb300/csrc/common.cuh"]
+                  "paper_1708_08640_gb300/csrc/common.cuh",
+                  "paper_1708_08640_gb300/csrc/kernels.h"]
 
 
 def parse():

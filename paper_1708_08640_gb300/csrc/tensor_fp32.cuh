@@ -315,108 +315,133 @@ struct CoreAcc {
     }
 };
 
-// One tile's core step added lock-free to the core in global memory: thread (q, slice) sums
-// its slice of the tile's entries for multi-index q and all JP values of the last mode, then
-// adds  sc * sum - rg * G  (rg only once, by slice 0) with atomics.
+// One tile's core step added lock-free to the core in global memory.  The multi-indices q
+// of the first N - 1 modes come in pairs (q, q + 1) that differ in mode N - 1's index; thread
+// (pair, slice) sums its slice of the tile's entries for both multi-indices and all JP values
+// of the last mode (the last mode's row is loaded once for the pair), slices 1.. hand their
+// sums to slice 0 through the stage (read by then), and slice 0 adds sc * sum - rg * G with
+// one atomic per element.
 template <int N, int JP, int ST = kTile, int T = kTile>
 struct CoreTile {
     static constexpr int JPR = round4(JP);
     static constexpr int Q = ipow_t<JP, N - 1>::v;
-    static constexpr int KS = (T / Q) > 0 ? (T / Q) : 1;
-    static constexpr int QPT = (Q + T - 1) / T;
+    static constexpr int JH2 = (JP + 1) / 2;     // pairs per row of mode N - 1 (padding is zero)
+    static constexpr int QP = Q / JP * JH2;      // pairs of multi-indices
+    static constexpr int KS0 = (T / QP) > 0 ? (T / QP) : 1;
+    static constexpr int KSM = 1 + (N * ST) / (2 * QP);   // slices whose sums fit in the stage
+    static constexpr int KS = KS0 < KSM ? KS0 : KSM;
+    static constexpr int QPT = (QP + T - 1) / T;
     // entries per step of the accumulation loop: their shared-memory loads are independent of
     // the accumulation chain, which keeps the entries' order
-    static constexpr int U = JP <= 16 ? 4 : (JP <= 20 ? 2 : 1);
-    // with several slices, slices 1.. hand their sums to slice 0 through the stage (read by
-    // then), so that one atomic per element reaches the core instead of KS
-    static constexpr bool kReduce = KS > 1 && (KS - 1) * Q * JPR <= N * ST * JPR;
+    static constexpr int U = JP <= 10 ? 4 : (JP <= 20 ? 2 : 1);
 
-    // thread (q, slice)'s sum over its slice of the tile's entries
-    __device__ __forceinline__ static void accumulate(const float* __restrict__ stage, int nb, int q,
-                                                      int slice, float (&tile)[JP]) {
+    // pair p's sums over slice `slice` of the tile's entries (b = slice, slice + KS, ...)
+    __device__ __forceinline__ static void accumulate(const float* __restrict__ stage, int nb, int p,
+                                                      int slice, float (&tile)[2][JP]) {
         int jj[N - 1];
+        jj[N - 2] = 2 * (p % JH2);
         {
-            int r = q;
+            int r = p / JH2;
 #pragma unroll
-            for (int n = N - 2; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
+            for (int n = N - 3; n >= 0; --n) { jj[n] = r % JP; r /= JP; }
         }
 #pragma unroll
-        for (int j = 0; j < JP; ++j) tile[j] = 0.f;
+        for (int j = 0; j < JP; ++j) { tile[0][j] = 0.f; tile[1][j] = 0.f; }
+        auto weights = [&](int b, float& wa, float& wb) {
+            float w = 1.f;
+#pragma unroll
+            for (int n = 0; n < N - 2; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
+            const float2 s = *reinterpret_cast<const float2*>(stage + ((N - 2) * ST + b) * JPR + jj[N - 2]);
+            wa = w * s.x;
+            wb = w * s.y;
+        };
         int b = slice;
         for (; b + (U - 1) * KS < nb; b += U * KS) {
-            float w[U], r[U][JP];
+            float wa[U], wb[U], r[U][JP];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int bu = b + u * KS;
-                w[u] = stage[(0 * ST + bu) * JPR + jj[0]];
-#pragma unroll
-                for (int n = 1; n < N - 1; ++n) w[u] *= stage[(n * ST + bu) * JPR + jj[n]];
-                load_grow<JP>(stage + ((N - 1) * ST + bu) * JPR, r[u]);
+                weights(b + u * KS, wa[u], wb[u]);
+                load_grow<JP>(stage + ((N - 1) * ST + b + u * KS) * JPR, r[u]);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
 #pragma unroll
-                for (int j = 0; j < JP; ++j) tile[j] = fmaf(w[u], r[u][j], tile[j]);
+                for (int j = 0; j < JP; ++j) {
+                    tile[0][j] = fmaf(wa[u], r[u][j], tile[0][j]);
+                    tile[1][j] = fmaf(wb[u], r[u][j], tile[1][j]);
+                }
         }
         for (; b < nb; b += KS) {
-            float w = stage[(0 * ST + b) * JPR + jj[0]];
-#pragma unroll
-            for (int n = 1; n < N - 1; ++n) w *= stage[(n * ST + b) * JPR + jj[n]];
-            float r[JP];
+            float wa, wb, r[JP];
+            weights(b, wa, wb);
             load_grow<JP>(stage + ((N - 1) * ST + b) * JPR, r);
 #pragma unroll
-            for (int j = 0; j < JP; ++j) tile[j] = fmaf(w, r[j], tile[j]);
+            for (int j = 0; j < JP; ++j) {
+                tile[0][j] = fmaf(wa, r[j], tile[0][j]);
+                tile[1][j] = fmaf(wb, r[j], tile[1][j]);
+            }
         }
     }
 
-    // G[q] += sc * tile - rg * G[q] (rg only when add_reg)
-    __device__ __forceinline__ static void add(float* G, const float* __restrict__ sG, int q,
-                                               const float (&tile)[JP], float sc, float rg,
-                                               bool add_reg) {
-        float g[JP];
-        load_grow<JP>(sG + q * JPR, g);
-        float d[JPR];
+    // G[q] += sc * tile - rg * G[q] for both multi-indices of pair p (the second only when it
+    // exists: JP odd pads the pair)
+    __device__ __forceinline__ static void add(float* G, const float* __restrict__ sG, int p,
+                                               const float (&tile)[2][JP], float sc, float rg) {
+        const int q0 = (p / JH2) * JP + 2 * (p % JH2);
 #pragma unroll
-        for (int j = 0; j < JPR; ++j) d[j] = j < JP ? fmaf(sc, tile[j], add_reg ? -rg * g[j] : 0.f) : 0.f;
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && 2 * (p % JH2) + 1 >= JP) break;
+            const int q = q0 + h;
+            float g[JP];
+            load_grow<JP>(sG + q * JPR, g);
+            float d[JPR];
 #pragma unroll
-        for (int c = 0; c < JPR / 4; ++c)
-            red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+            for (int j = 0; j < JPR; ++j) d[j] = j < JP ? fmaf(sc, tile[h][j], -rg * g[j]) : 0.f;
+#pragma unroll
+            for (int c = 0; c < JPR / 4; ++c)
+                red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+        }
     }
 
-    // Every one of the T threads calls apply (it has CTA barriers over T threads when
-    // kReduce; the stage is overwritten then).
+    // Every one of the T threads calls apply (with several slices it has CTA barriers over
+    // T threads, and the stage is overwritten).
     __device__ __forceinline__ static void apply(float* stage, int nb, const float* __restrict__ sG,
                                                  float* G, float sc, float rg) {
         const int t = threadIdx.x;
-        const int slice = KS > 1 ? t / Q : 0;
-        if constexpr (kReduce) {
-            const int q = t % Q;
+        if constexpr (KS > 1) {
+            const int p = t % QP, slice = t / QP;
             const bool act = slice < KS;
-            float tile[JP];
-            if (act) accumulate(stage, nb, q, slice, tile);
+            float tile[2][JP];
+            if (act) accumulate(stage, nb, p, slice, tile);
             asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
             if (act && slice > 0) {
-                float* o = stage + ((slice - 1) * Q + q) * JPR;
+                float* o = stage + ((slice - 1) * QP + p) * 2 * JPR;
 #pragma unroll
-                for (int j = 0; j < JP; ++j) o[j] = tile[j];
+                for (int j = 0; j < JP; ++j) {
+                    o[j] = tile[0][j];
+                    o[JPR + j] = tile[1][j];
+                }
             }
             asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
             if (act && slice == 0) {
                 for (int sl = 1; sl < KS; ++sl) {
-                    const float* o = stage + ((sl - 1) * Q + q) * JPR;
+                    const float* o = stage + ((sl - 1) * QP + p) * 2 * JPR;
 #pragma unroll
-                    for (int j = 0; j < JP; ++j) tile[j] += o[j];
+                    for (int j = 0; j < JP; ++j) {
+                        tile[0][j] += o[j];
+                        tile[1][j] += o[JPR + j];
+                    }
                 }
-                add(G, sG, q, tile, sc, rg, true);
+                add(G, sG, p, tile, sc, rg);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < QPT; ++k) {
-                const int q = KS > 1 ? (t % Q) : (t + k * T);
-                if (slice >= KS || q >= Q) continue;
-                float tile[JP];
-                accumulate(stage, nb, q, slice, tile);
-                add(G, sG, q, tile, sc, rg, slice == 0);
+                const int p = t + k * T;
+                if (p >= QP) continue;
+                float tile[2][JP];
+                accumulate(stage, nb, p, 0, tile);
+                add(G, sG, p, tile, sc, rg);
             }
         }
     }
