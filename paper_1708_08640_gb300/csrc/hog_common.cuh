@@ -122,10 +122,11 @@ __device__ __forceinline__ void hog_tables(const DGroup& Gr, int64_t t, float* s
 }
 
 // Eq. (8), coupled rows, for one coupled entry of matrix m (row u of U^(c), column k of
-// V_m, value y) whose rows were gathered already: the gradients to slots pu and pv
+// V_m with kinv = 1 / |Omega_Y^{2,k}|, value y) whose rows were gathered already: the
+// gradients to slots pu and pv
 template <int JP>
 __device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, const HogSmem& H,
-                                                int m, int k, int32_t pu, int32_t pv, float y,
+                                                int m, float kinv, int32_t pu, int32_t pv, float y,
                                                 const float (&u)[JP], const float (&v)[JP]) {
     constexpr int JPR = round4(JP);
     float yh = 0.f;
@@ -133,7 +134,7 @@ __device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, c
     for (int j = 0; j < JP; ++j) yh = fmaf(u[j], v[j], yh);
     const float lm = P.lambda_m;
     const float err = y - yh;
-    const float rv = lm * P.lambda_reg * __ldg(P.inv_cnt[P.N + m] + k);
+    const float rv = lm * P.lambda_reg * kinv;
     float du[JPR], dv[JPR];
 #pragma unroll
     for (int j = 0; j < JPR; ++j) {

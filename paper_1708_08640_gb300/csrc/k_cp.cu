@@ -52,12 +52,14 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
         for (int j = 0; j < JP; ++j) gd[j] = 0.f;
         if (tid < nb) {
             const int64_t e = e0 + tid;
-            float a[N][JP];
-            int32_t row[N];
+            float a[N][JP], inv[N];
+            int32_t tp[N];
 #pragma unroll
             for (int n = 0; n < N; ++n) {
-                row[n] = __ldg(Gr.tidx[n] + e);
-                load_row<JP, true>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
+                const int32_t row = __ldg(Gr.tidx[n] + e);
+                tp[n] = __ldg(Gr.tpos[n] + e);
+                load_row<JP, true>(P.U[n] + (int64_t)row * JPR, a[n]);
+                inv[n] = __ldg(P.inv_cnt[n] + row);
             }
             float prod[JP];
             float xt = 0.f;
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
             const float err = __ldg(Gr.tval + e) - xt;
 #pragma unroll
             for (int n = 0; n < N; ++n) {
-                const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                const float r = P.lambda_reg * inv[n];
                 float c[JPR];
 #pragma unroll
                 for (int j = 0; j < JPR; ++j) {
@@ -85,7 +87,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
                     }
                     c[j] = j < JP ? fmaf(-err, pn, r * a[n][j]) : 0.f;
                 }
-                put_slot<JPR>(smem, H, n, __ldg(Gr.tpos[n] + e), c);
+                put_slot<JPR>(smem, H, n, tp[n], c);
             }
 #pragma unroll
             for (int j = 0; j < JP; ++j) gd[j] = err * prod[j];

@@ -153,15 +153,23 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         const bool valid = tid < nb;
         const int64_t e = e0 + tid;
         float a1[JP], a2[JP], a3[JP];
-        int32_t row[3] = {0, 0, 0};
         float x = 0.f;
+        // the rows' 1 / |Omega^{n,i}| and the entry's slot positions, loaded with the rows
+        // (they are used after the MMAs)
+        float inv[3] = {0.f, 0.f, 0.f};
+        int32_t tp[3] = {0, 0, 0};
         if (valid) {
-            row[0] = __ldg(Gr.tidx[0] + e);
-            row[1] = __ldg(Gr.tidx[1] + e);
-            row[2] = __ldg(Gr.tidx[2] + e);
+            int32_t row[3];
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                row[n] = __ldg(Gr.tidx[n] + e);
+                tp[n] = __ldg(Gr.tpos[n] + e);
+            }
             load_row_ld<JP>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
             load_row_ld<JP>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
             load_row_ld<JP>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
+#pragma unroll
+            for (int n = 0; n < 3; ++n) inv[n] = __ldg(P.inv_cnt[n] + row[n]);
             x = __ldg(Gr.tval + e);
         } else {
 #pragma unroll
@@ -317,19 +325,19 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 for (int i = 0; i < 16; ++i) p3[16 * h + i] = v[i];
             }
             if (valid) {
-                const float r0 = P.lambda_reg * __ldg(P.inv_cnt[0] + row[0]);
-                const float r1 = P.lambda_reg * __ldg(P.inv_cnt[1] + row[1]);
-                const float r2 = P.lambda_reg * __ldg(P.inv_cnt[2] + row[2]);
+                const float r0 = P.lambda_reg * inv[0];
+                const float r1 = P.lambda_reg * inv[1];
+                const float r2 = P.lambda_reg * inv[2];
                 float c[JPR];
 #pragma unroll
                 for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p1[j], r0 * a1[j]);
-                put_slot<JPR>(smem, H, 0, __ldg(Gr.tpos[0] + e), c);
+                put_slot<JPR>(smem, H, 0, tp[0], c);
 #pragma unroll
                 for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p2[j], r1 * a2[j]);
-                put_slot<JPR>(smem, H, 1, __ldg(Gr.tpos[1] + e), c);
+                put_slot<JPR>(smem, H, 1, tp[1], c);
 #pragma unroll
                 for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
-                put_slot<JPR>(smem, H, 2, __ldg(Gr.tpos[2] + e), c);
+                put_slot<JPR>(smem, H, 2, tp[2], c);
             }
         }
         hog_coupled<JP>(P, Gr, t, smem, H, tid, kBfTile);

@@ -122,23 +122,26 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             // the first round of coupled entries: indices from the buffer, rows gathered now
             const bool hc = kEarlyCpl && tid < nc;
             float cu[kEarlyCpl ? JP : 1], cv[kEarlyCpl ? JP : 1];
-            int cm = 0, ck = 0;
+            int cm = 0;
+            float cinv = 0.f;   // 1 / |Omega_Y^{2,k}| of the entry's column, loaded with its rows
             if constexpr (kEarlyCpl) {
                 if (hc) {
                     cm = mb[M.c_m + tid];
-                    ck = mb[M.c_k + tid];
+                    const int ck = mb[M.c_k + tid];
                     load_row<JP, true>(P.U[P.cmode[cm]] + (int64_t)mb[M.c_r + tid] * JPR, cu);
                     load_row<JP, true>(P.V[cm] + (int64_t)ck * JPR, cv);
+                    cinv = __ldg(P.inv_cnt[P.N + cm] + ck);
                 }
             }
             if constexpr (L == 1) {
                 float a[N][JP];
-                int32_t row[N];
+                float inv[N];   // 1 / |Omega^{n,i}| of the entry's rows, loaded with the rows
                 if (tid < nb) {
 #pragma unroll
                     for (int n = 0; n < N; ++n) {
-                        row[n] = mb[M.tidx + n * ST + tid];
-                        load_row<JP, true>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
+                        const int32_t row = mb[M.tidx + n * ST + tid];
+                        load_row<JP, true>(P.U[n] + (int64_t)row * JPR, a[n]);
+                        inv[n] = __ldg(P.inv_cnt[n] + row);
                     }
                 }
                 reload_core();
@@ -147,7 +150,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                     const float err = __int_as_float(mb[M.tval + tid]) - entry_partials<N, JP>(sG, a, p);
 #pragma unroll
                     for (int n = 0; n < N; ++n) {
-                        const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                        const float r = P.lambda_reg * inv[n];
                         float c[JPR];
 #pragma unroll
                         for (int j = 0; j < JPR; ++j) c[j] = j < JP ? fmaf(-err, p[n][j], r * a[n][j]) : 0.f;
@@ -164,6 +167,9 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                 int32_t row[3] = {0, 0, 0};
                 float a1s[JH], a2[JP], a3[JP];
                 float x = 0.f;
+                // 1 / |Omega^{n,i}| of mode 1's row and of the row this lane writes in modes 2
+                // or 3, loaded with the rows
+                float inv1 = 0.f, inv23 = 0.f;
                 const int j1base = lsub * JH;
                 if (valid) {
 #pragma unroll
@@ -173,6 +179,8 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                     for (int jj = 0; jj < JH; ++jj) a1s[jj] = j1base + jj < JP ? __ldcg(u1 + j1base + jj) : 0.f;
                     load_row<JP, true>(P.U[1] + (int64_t)row[1] * JPR, a2);
                     load_row<JP, true>(P.U[2] + (int64_t)row[2] * JPR, a3);
+                    inv1 = __ldg(P.inv_cnt[0] + row[0]);
+                    if (lsub < 2) inv23 = lsub == 0 ? __ldg(P.inv_cnt[1] + row[1]) : __ldg(P.inv_cnt[2] + row[2]);
                     x = __int_as_float(mb[M.tval + sl]);
                 } else {
 #pragma unroll
@@ -196,7 +204,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                     const float err = x - xt;
                     // mode 1: this lane's j1 values (the slot's padding is written by the last lane)
                     {
-                        const float r = P.lambda_reg * __ldg(P.inv_cnt[0] + row[0]);
+                        const float r = P.lambda_reg * inv1;
                         float* sa = smem + H.off[0] + mb[M.tpos + sl] * slot_stride(JPR);
                         float* sp = stage + (0 * ST + slot) * JPR;
 #pragma unroll
@@ -217,7 +225,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                         // (element-wise selects: a pointer to either register array would move
                         // both arrays to local memory)
                         const int n = 1 + lsub;
-                        const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
+                        const float r = P.lambda_reg * inv23;
                         float c[JPR];
                         float* sp = stage + (n * ST + slot) * JPR;
 #pragma unroll
@@ -234,7 +242,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             // coupled entries, Eq. (8): the first round from the rows gathered above, then
             // any further rounds in full
             if constexpr (kEarlyCpl) {
-                if (hc) hog_coupled_one<JP>(P, smem, H, cm, ck, mb[M.c_pu + tid], mb[M.c_pv + tid],
+                if (hc) hog_coupled_one<JP>(P, smem, H, cm, cinv, mb[M.c_pu + tid], mb[M.c_pv + tid],
                                             __int_as_float(mb[M.c_y + tid]), cu, cv);
             }
             for (int e = kEarlyCpl ? tid + kT : tid; e < nc; e += kT) {
@@ -242,7 +250,8 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                 const int m = mb[M.c_m + e], k = mb[M.c_k + e];
                 load_row<JP, true>(P.U[P.cmode[m]] + (int64_t)mb[M.c_r + e] * JPR, u);
                 load_row<JP, true>(P.V[m] + (int64_t)k * JPR, v);
-                hog_coupled_one<JP>(P, smem, H, m, k, mb[M.c_pu + e], mb[M.c_pv + e],
+                const float kinv = __ldg(P.inv_cnt[P.N + m] + k);
+                hog_coupled_one<JP>(P, smem, H, m, kinv, mb[M.c_pu + e], mb[M.c_pv + e],
                                     __int_as_float(mb[M.c_y + e]), u, v);
             }
             compute_barrier<kT>();
