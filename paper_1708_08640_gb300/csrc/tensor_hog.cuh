@@ -255,6 +255,9 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                                     __int_as_float(mb[M.c_y + e]), u, v);
             }
             compute_barrier<kT>();
+            // the row steps first: their reductions drain while the core step computes, not in
+            // front of the next tile's gathers
+            hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kT);
             // core: this tile's share of the core step,
             //   G += eta * cs / W * (sum_b e_b a1 o..o aN / n_t - lambda_reg / |Omega| * G)
             if (nb > 0) {
@@ -262,7 +265,6 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
                 const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
                 CoreTile<N, JP, ST, kT>::apply(stage, nb, sG, P.G, sc, rg);
             }
-            hog_flush_meta<JPR>(P, smem, H, mb, eta, row_mean, tid, kT);
         }
         tile_barrier<kT>();
     }
