@@ -88,10 +88,14 @@ typedef struct {
     float core_scale;   /* core step = eta_t * core_scale * (mean core gradient of a group) */
     int row_rule;       /* S3_ROW_SUM or S3_ROW_MEAN: a row takes the sum, or the mean, of
                            its gradients within one group (batch or HOGWILD tile) */
-    int hog_tile;       /* HOGWILD: tensor entries per tile of the FP32 kernel (0 = default:
-                           96 for 3-way tensors, at most 128, and tiles of up to 64 entries
-                           spread each entry over four threads; 256 for 4-way); the BF16
-                           kernel's tiles hold 128 */
+    int hog_tile;       /* HOGWILD: tensor entries per tile of the FP32 kernel.  Its CTAs have
+                           T compute threads, T = 384 for 3-way tensors up to padded rank 16
+                           and 256 otherwise; a 3-way tile holds at most T / 2 entries (two
+                           threads per entry; tiles of up to T / 4 spread each entry over
+                           four), a 4-way tile T.  0 = default: T / 2 for 3-way tensors up to
+                           rank 20 (192 at rank 10), 64 above, 128 with cp = 1, T for 4-way.
+                           The BF16 kernel's tiles (at most 128) are sized to hold as many
+                           entries in flight as the FP32 form. */
     float hog_staleness;/* HOGWILD: gamma of the staleness-aware row step.  A row expected to
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by

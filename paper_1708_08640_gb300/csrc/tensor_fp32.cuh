@@ -318,18 +318,21 @@ struct CoreAcc {
 // One tile's core step added lock-free to the core in global memory.  The multi-indices q
 // of the first N - 1 modes come in pairs (q, q + 1) that differ in mode N - 1's index; thread
 // (pair, slice) sums its slice of the tile's entries for both multi-indices and all JP values
-// of the last mode (the last mode's row is loaded once for the pair), slices 1.. hand their
-// sums to slice 0 through the stage (read by then), and slice 0 adds sc * sum - rg * G with
-// one atomic per element.
+// of the last mode (the last mode's row is loaded once for the pair).  With several slices,
+// every slice leaves its sums in the stage (read by then), and then every thread takes
+// (multi-index, 4 values of the last mode) items: the slices' sums in slice order, and
+// sc * sum - rg * G added with one atomic.
 template <int N, int JP, int ST = kTile, int T = kTile>
 struct CoreTile {
     static constexpr int JPR = round4(JP);
     static constexpr int Q = ipow_t<JP, N - 1>::v;
     static constexpr int JH2 = (JP + 1) / 2;     // pairs per row of mode N - 1 (padding is zero)
     static constexpr int QP = Q / JP * JH2;      // pairs of multi-indices
-    static constexpr int KS0 = (T / QP) > 0 ? (T / QP) : 1;
-    static constexpr int KSM = 1 + (N * ST) / (2 * QP);   // slices whose sums fit in the stage
-    static constexpr int KS = KS0 < KSM ? KS0 : KSM;
+    // slices: enough threads, at most 16 (each item of the final sum reads one per slice),
+    // and as many as leave their sums in the stage
+    static constexpr int KS0 = (T / QP) > 16 ? 16 : ((T / QP) > 0 ? (T / QP) : 1);
+    static constexpr int KSM = (N * ST) / (2 * QP);
+    static constexpr int KS = KS0 < KSM ? KS0 : (KSM > 1 ? KSM : 1);
     static constexpr int QPT = (QP + T - 1) / T;
     // entries per step of the accumulation loop: their shared-memory loads are independent of
     // the accumulation chain, which keeps the entries' order
@@ -409,30 +412,38 @@ struct CoreTile {
                                                  float* G, float sc, float rg) {
         const int t = threadIdx.x;
         if constexpr (KS > 1) {
+            // (every thread reaches each barrier at the same instruction: warps can straddle
+            // the last slice)
             const int p = t % QP, slice = t / QP;
             const bool act = slice < KS;
             float tile[2][JP];
             if (act) accumulate(stage, nb, p, slice, tile);
             asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
-            if (act && slice > 0) {
-                float* o = stage + ((slice - 1) * QP + p) * 2 * JPR;
+            if (act) {
+                float* o = stage + (slice * QP + p) * 2 * JPR;
 #pragma unroll
-                for (int j = 0; j < JP; ++j) {
-                    o[j] = tile[0][j];
-                    o[JPR + j] = tile[1][j];
+                for (int j = 0; j < JPR; ++j) {
+                    o[j] = j < JP ? tile[0][j] : 0.f;
+                    o[JPR + j] = j < JP ? tile[1][j] : 0.f;
                 }
             }
             asm volatile("bar.sync 1, %0;" :: "r"(T) : "memory");
-            if (act && slice == 0) {
+            for (int i = t; i < Q * (JPR / 4); i += T) {
+                const int q = i / (JPR / 4), c = i % (JPR / 4);
+                const int jl = q % JP;
+                const int pp = (q / JP) * JH2 + jl / 2;
+                const float* o = stage + (pp * 2 + (jl & 1)) * JPR + 4 * c;
+                float4 acc = *reinterpret_cast<const float4*>(o);
                 for (int sl = 1; sl < KS; ++sl) {
-                    const float* o = stage + ((sl - 1) * QP + p) * 2 * JPR;
-#pragma unroll
-                    for (int j = 0; j < JP; ++j) {
-                        tile[0][j] += o[j];
-                        tile[1][j] += o[JPR + j];
-                    }
+                    const float4 v = *reinterpret_cast<const float4*>(o + sl * QP * 2 * JPR);
+                    acc.x += v.x;
+                    acc.y += v.y;
+                    acc.z += v.z;
+                    acc.w += v.w;
                 }
-                add(G, sG, p, tile, sc, rg);
+                const float4 g = *reinterpret_cast<const float4*>(sG + q * JPR + 4 * c);
+                red_add_v4(G + q * JPR + 4 * c, fmaf(sc, acc.x, -rg * g.x), fmaf(sc, acc.y, -rg * g.y),
+                           fmaf(sc, acc.z, -rg * g.z), fmaf(sc, acc.w, -rg * g.w));
             }
         } else {
 #pragma unroll
