@@ -293,7 +293,7 @@ def run_reference(args, world, rank):
 # ----------------------------------------------------------------------------- forms
 def precision_forms(p, order, stream, args, J=16, epochs=4):
     """The FP32 and BF16 forms of the HOGWILD epoch on the same data at rank J (the cfg2
-    workloads, J = 16 and 32): epoch time, nnz-updates/s, test RMSE after every epoch (the
+    workloads, J = 16 and 32, and the cfg1 data at J = 10 and 20): epoch time, nnz-updates/s, test RMSE after every epoch (the
     "matched RMSE" check: the largest relative gap between the two forms' curves), and the
     tensor-pass kernel's roofline (FP32 FFMA roof for the FP32 form, BF16 tensor roof for
     the BF16 form).  Epochs are timed one by one with CUDA events; the RMSE reads between
@@ -696,6 +696,7 @@ def run_ours(args, world, rank, local):
         extras["cp_hogwild"] = cp_hogwild(p, order, stream)
         extras["forms_j10"] = precision_forms(p, order, stream, args, J=10)
         extras["forms_j16"] = precision_forms(p, order, stream, args, J=16)
+        extras["forms_j20"] = precision_forms(p, order, stream, args, J=20, epochs=3)
         extras["forms_j32"] = precision_forms(p, order, stream, args, J=32, epochs=2)
 
     # ---- end to end through the public API with host buffers

@@ -57,7 +57,7 @@ struct s3_ctx {
     float* inv_cnt[kMaxF] = {};
     int64_t hog_grid = 1;
     int64_t hog_bf_grid = 0;        // BF16 HOGWILD CTAs (0: the form is not available)
-    int bf_jp = 16;                 // the rank the BF16 form computes at (16 or 32)
+    int bf_jp = 16;                 // the rank the BF16 form computes at (16, 20 or 32)
     size_t cp_smem = 0;             // S3CMTF-CP kernel's dynamic shared memory
     size_t hog_bf_smem = 0;
     int64_t hog_tile = 0, hog_per_sm = 0, hog_bf_per_sm = 0, hog_bf_tile = 0, hog_ccap = 0;
@@ -416,7 +416,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // the BF16 form computes at rank 16 or 32 (the tensor cores' granularity), zero-extending
     // the context's layout
     const bool bf16_ok = N == 3 && ctx->JP <= 32;
-    ctx->bf_jp = ctx->JP <= 16 ? 16 : 32;
+    ctx->bf_jp = ctx->JP <= 16 ? 16 : (ctx->JP == 20 ? 20 : 32);
     std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb, kShortSeg);
     if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SLOT, hhog);
     // HOGWILD concurrency of the FP32 form: CTAs resident at once, each on a tile of `tile`

@@ -1,6 +1,7 @@
-// BF16 tensor-core form of the S3CMTF tensor pass (3-way, ranks up to 32 computed at JP = 16
-// or 32), sm_103a.  The parameters keep the context's FP32 layout (rows of P.ld floats, the
-// core P.jp x P.jp x P.ldg); the kernel zero-extends them to JP.
+// BF16 tensor-core form of the S3CMTF tensor pass (3-way, ranks up to 32), sm_103a.  A
+// kernel variant computes on a JQ x JQ grid of (j1, j2) pairs and a last-mode rank JK:
+// (16, 16), (20, 32) or (32, 32) (see BfLayout).  The parameters keep the context's FP32
+// layout (rows of P.ld floats, the core P.jp x P.jp x P.ldg); the kernel zero-extends them.
 //
 // A CTA of 128 threads takes tiles of 128 tensor entries (the MMA's M), one entry per
 // thread and TMEM lane.  The three dense contractions of the per-entry work run on the
@@ -8,15 +9,15 @@
 // accumulators in tensor memory), chunk by chunk of 128 (j1, j2) pairs:
 //   stage 1   T  = A3 . G_(3)^T      [128 entries x 128 pairs]   (Def. 4, Alg. 3: the core
 //                                      contracted with the last mode's rows)
-//   partial   P3 = KR . G_(3)        [128 entries x JP]           (p_3 = G x_{-3} {a})
-//   core      dG = KR^T . (e o A3)   [128 pairs x JP]             (sum_b e_b a1 o a2 o a3)
+//   partial   P3 = KR . G_(3)        [128 entries x JK]           (p_3 = G x_{-3} {a})
+//   core      dG = KR^T . (e o A3)   [128 pairs x JK]             (sum_b e_b a1 o a2 o a3)
 // with KR[b] = a1_b (x) a2_b (the Khatri-Rao row of the entry).  The rest runs on CUDA cores
 // in FP32: p_1 = T a_2, p_2 = T^T a_1 and x~ = a_1 . p_1 from each thread's TMEM lane, the
 // error e = x - x~, the row gradients of Eq. (8) and the row / core steps.  FP32 master
 // parameters; BF16 only for the tensor-core operands.
 //
 // Shared-memory operands (no swizzle, 8 x 16-byte core matrices; see tc.cuh):
-//   sG   the core, element (j3, pair) at (pair/8)*(JP/8)*128 + (j3/8)*128 + (j3%8)*16
+//   sG   the core, element (j3, pair) at (pair/8)*(JK/8)*128 + (j3/8)*128 + (j3%8)*16
 //        + (pair%8)*2: MN-major B of stage 1 (K = j3, N = pair) and K-major B of the
 //        partial (K = pair, N = j3), both read from the same bytes
 //   sA3  K-major A of stage 1 (M = entry, K = j3)
@@ -24,7 +25,7 @@
 //        MN-major, the A operand of the core GEMM (M = pair, K = entry)
 //   sEA3 e*a3, MN-major B of the core GEMM (K = entry, N = j3)
 // TMEM (256 columns, so that two CTAs share an SM): T of one chunk [0, 128), P3
-// [128, 128 + JP), dG of one chunk [128 + JP, 128 + 2 JP).
+// [128, 128 + JK), dG of one chunk [128 + JK, 128 + 2 JK).
 #include <cuda_runtime.h>
 
 #include "hog_common.cuh"
@@ -41,15 +42,21 @@ constexpr uint32_t kTmemCols = 256;
 // columns) are ever resident on one SM
 constexpr size_t kBfMinSmem = 80 * 1024;
 
-template <int JP>
+// JQ: the side of the (j1, j2) pair grid (the rank of modes 1 and 2 the kernel computes
+// at); JK: the last mode's rank, padded to the MMAs' K and N granularity.  (16, 16) and
+// (32, 32) for padded ranks up to 16 and 32; (20, 20 x 20 pairs, j3 padded to 32) for
+// rank 20, whose pairs (padded to whole chunks of 128) cost half those of (32, 32).
+template <int JQ, int JK>
 struct BfLayout {
-    static_assert(JP == 16 || JP == 32, "the BF16 form is built for padded ranks 16 and 32");
-    static constexpr int NPAIR = JP * JP;
+    static_assert((JQ == 16 && JK == 16) || (JQ == 20 && JK == 32) || (JQ == 32 && JK == 32),
+                  "the BF16 form is built for padded ranks 16, 20 and 32");
+    static constexpr int NQ = JQ * JQ;                                  // pairs of the grid
+    static constexpr int NPAIR = (NQ + kChunk - 1) / kChunk * kChunk;   // in whole chunks
     static constexpr int NC = NPAIR / kChunk;
-    static constexpr uint32_t G_BYTES = JP * NPAIR * 2;
-    static constexpr uint32_t A3_BYTES = kBfTile * JP * 2;
+    static constexpr uint32_t G_BYTES = JK * NPAIR * 2;
+    static constexpr uint32_t A3_BYTES = kBfTile * JK * 2;
     static constexpr uint32_t KR_BYTES = kBfTile * kChunk * 2;
-    static constexpr uint32_t EA3_BYTES = kBfTile * JP * 2;
+    static constexpr uint32_t EA3_BYTES = kBfTile * JK * 2;
     static constexpr uint32_t OFF_G = 0;
     static constexpr uint32_t OFF_A3 = OFF_G + G_BYTES;
     static constexpr uint32_t OFF_KR = OFF_A3 + A3_BYTES;
@@ -57,8 +64,8 @@ struct BfLayout {
     static constexpr uint32_t OFF_SLOTS = OFF_EA3 + EA3_BYTES;   // row gradient slots (floats)
     static constexpr uint32_t COL_T = 0;
     static constexpr uint32_t COL_P3 = kChunk;
-    static constexpr uint32_t COL_DG = kChunk + JP;
-    static_assert(COL_DG + JP <= kTmemCols, "TMEM budget");
+    static constexpr uint32_t COL_DG = kChunk + JK;
+    static_assert(COL_DG + JK <= kTmemCols, "TMEM budget");
     static_assert(OFF_SLOTS % 16 == 0, "slot rows are written with 16-byte stores");
 };
 
@@ -70,17 +77,18 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 }
 
 // byte offset of core element (j3, pair) in sG
-template <int JP>
+template <int JK>
 __device__ __forceinline__ uint32_t g_off(int pair, int j3) {
-    return (uint32_t)((pair / 8) * (JP / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16 + (pair % 8) * 2);
+    return (uint32_t)((pair / 8) * (JK / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16 + (pair % 8) * 2);
 }
 
-template <int JP>
+template <int JQ, int JK>
 __global__ void __launch_bounds__(kBfTile, 2)
 k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, const float* eta_p,
                   int row_mean, float core_step_scale, HogSmem H, int* err_flag) {
-    using Lt = BfLayout<JP>;
-    constexpr int JPR = JP;          // JP is a multiple of 4
+    using Lt = BfLayout<JQ, JK>;
+    constexpr int JPR = JQ;          // slot rows (JQ is a multiple of 4)
+    constexpr int NQ = Lt::NQ;
     constexpr int NC = Lt::NC;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
@@ -122,16 +130,16 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         hog_tables(Gr, t, smem, H, tid, kBfTile);
         // ---- the current core as BF16 operand: coalesced float4 reads of G (the layout's
         //      jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix
-        //      layout (pair = j1 JP + j2); the padding past jp stays zero
-        if (P.jp == JP && P.ldg == JP) {
-            // the layout's rank is the kernel's: pair = l / JP with compile-time divisions
-            for (int l = tid * 4; l < Lt::NPAIR * JP; l += kBfTile * 4) {
+        //      layout (pair = j1 JQ + j2); the padding past jp stays zero
+        if (P.jp == JQ && P.ldg == JQ) {
+            // the layout's rank is the kernel's: pair = l / JQ with compile-time divisions
+            for (int l = tid * 4; l < NQ * JQ; l += kBfTile * 4) {
                 const float4 v = ld4_cg(P.G + l);
-                const int pair = l / JP, j0 = l % JP;
+                const int pair = l / JQ, j0 = l % JQ;
                 const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j0 + i)) =
+                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JK>(pair, j0 + i)) =
                         __float2bfloat16_rn(vv[i]);
             }
         } else {
@@ -139,11 +147,11 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             for (int l = tid * 4; l < jp * jp * ldg; l += kBfTile * 4) {
                 const float4 v = ld4_cg(P.G + l);
                 const int j3 = l % ldg, j12 = l / ldg;
-                const int pair = (j12 / jp) * JP + j12 % jp;
+                const int pair = (j12 / jp) * JQ + j12 % jp;
                 const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JP>(pair, j3 + i)) =
+                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JK>(pair, j3 + i)) =
                         __float2bfloat16_rn(vv[i]);
             }
         }
@@ -152,7 +160,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         const int nb = (int)(Gr.t_off[t + 1] - e0);
         const bool valid = tid < nb;
         const int64_t e = e0 + tid;
-        float a1[JP], a2[JP], a3[JP];
+        float a1[JQ], a2[JQ], a3[JK];
         float x = 0.f;
         // the rows' 1 / |Omega^{n,i}| and the entry's slot positions, loaded with the rows
         // (they are used after the MMAs)
@@ -165,20 +173,22 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 row[n] = __ldg(Gr.tidx[n] + e);
                 tp[n] = __ldg(Gr.tpos[n] + e);
             }
-            load_row_ld<JP>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
-            load_row_ld<JP>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
-            load_row_ld<JP>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
+            load_row_ld<JQ>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
+            load_row_ld<JQ>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
+            load_row_ld<JK>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
 #pragma unroll
             for (int n = 0; n < 3; ++n) inv[n] = __ldg(P.inv_cnt[n] + row[n]);
             x = __ldg(Gr.tval + e);
         } else {
 #pragma unroll
-            for (int j = 0; j < JP; ++j) { a1[j] = 0.f; a2[j] = 0.f; a3[j] = 0.f; }
+            for (int j = 0; j < JQ; ++j) { a1[j] = 0.f; a2[j] = 0.f; }
+#pragma unroll
+            for (int j = 0; j < JK; ++j) a3[j] = 0.f;
         }
         // A3 row (K-major, M = entry)
 #pragma unroll
-        for (int kg = 0; kg < JP / 8; ++kg) {
-            const uint32_t off = (tid / 8) * (JP / 8) * 128 + kg * 128 + (tid % 8) * 16;
+        for (int kg = 0; kg < JK / 8; ++kg) {
+            const uint32_t off = (tid / 8) * (JK / 8) * 128 + kg * 128 + (tid % 8) * 16;
             st_shared_v4(sA3 + off, pack_bf16x2(a3[8 * kg], a3[8 * kg + 1]),
                          pack_bf16x2(a3[8 * kg + 2], a3[8 * kg + 3]),
                          pack_bf16x2(a3[8 * kg + 4], a3[8 * kg + 5]),
@@ -188,19 +198,19 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         tc_fence_before();
         __syncthreads();
         // ---- stage 1, chunk by chunk; p1 and p2 from this thread's lane of T
-        float p1[JP], p2[JP];
+        float p1[JQ], p2[JQ];
 #pragma unroll
-        for (int j = 0; j < JP; ++j) { p1[j] = 0.f; p2[j] = 0.f; }
+        for (int j = 0; j < JQ; ++j) { p1[j] = 0.f; p2[j] = 0.f; }
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             if (tid == 0) {
                 tc_fence_after();
                 constexpr uint32_t idesc = tc_idesc_bf16(128, kChunk, 0, 1);
 #pragma unroll
-                for (int ks = 0; ks < JP / 16; ++ks) {
-                    const uint64_t ad = tc_sdesc(sA3 + ks * 256, 128, (JP / 8) * 128);
-                    const uint64_t bd = tc_sdesc(sG + (kChunk / 8) * c * (JP / 8) * 128 + ks * 256,
-                                                 128, (JP / 8) * 128);
+                for (int ks = 0; ks < JK / 16; ++ks) {
+                    const uint64_t ad = tc_sdesc(sA3 + ks * 256, 128, (JK / 8) * 128);
+                    const uint64_t bd = tc_sdesc(sG + (kChunk / 8) * c * (JK / 8) * 128 + ks * 256,
+                                                 128, (JK / 8) * 128);
                     tc_mma(tmem + Lt::COL_T, ad, bd, idesc, ks > 0);
                 }
                 tc_commit(&s_mbar);
@@ -215,7 +225,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
 #pragma unroll
                 for (int i = 0; i < 32; ++i) {
                     const int pair = kChunk * c + 32 * q + i;
-                    const int j1 = pair / JP, j2 = pair % JP;
+                    if (pair >= NQ) continue;   // past the grid (its T is zero)
+                    const int j1 = pair / JQ, j2 = pair % JQ;
                     p1[j1] = fmaf(v[i], a2[j2], p1[j1]);
                     p2[j2] = fmaf(v[i], a1[j1], p2[j2]);
                 }
@@ -226,11 +237,11 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         }
         float xt = 0.f;
 #pragma unroll
-        for (int j = 0; j < JP; ++j) xt = fmaf(a1[j], p1[j], xt);
+        for (int j = 0; j < JQ; ++j) xt = fmaf(a1[j], p1[j], xt);
         const float err = valid ? x - xt : 0.f;
         // e * a3 (MN-major B of the core GEMM: K = entry, N = j3)
 #pragma unroll
-        for (int jg = 0; jg < JP / 8; ++jg) {
+        for (int jg = 0; jg < JK / 8; ++jg) {
             const uint32_t off = jg * (kBfTile / 8) * 128 + (tid / 8) * 128 + (tid % 8) * 16;
             st_shared_v4(sEA3 + off, pack_bf16x2(err * a3[8 * jg], err * a3[8 * jg + 1]),
                          pack_bf16x2(err * a3[8 * jg + 2], err * a3[8 * jg + 3]),
@@ -250,7 +261,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const int pair = kChunk * c + 8 * kg + i;
-                    w[i] = a1[pair / JP] * a2[pair % JP];
+                    const int pq = pair < NQ ? pair : 0;   // (a compile-time index)
+                    w[i] = pair < NQ ? a1[pq / JQ] * a2[pq % JQ] : 0.f;
                 }
                 const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
                 st_shared_v4(sKR + off, pack_bf16x2(w[0], w[1]), pack_bf16x2(w[2], w[3]),
@@ -261,17 +273,17 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
-                // P3 += KR . G_(3)[chunk]   (M = 128 entries, N = JP, K = 128 pairs)
-                constexpr uint32_t id_p3 = tc_idesc_bf16(128, JP, 0, 0);
+                // P3 += KR . G_(3)[chunk]   (M = 128 entries, N = JK, K = 128 pairs)
+                constexpr uint32_t id_p3 = tc_idesc_bf16(128, JK, 0, 0);
 #pragma unroll
                 for (int ks = 0; ks < kChunk / 16; ++ks) {
                     const uint64_t ad = tc_sdesc(sKR + ks * 256, 128, (kChunk / 8) * 128);
-                    const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JP / 8) * 128,
-                                                 (JP / 8) * 128, 128);
+                    const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JK / 8) * 128,
+                                                 (JK / 8) * 128, 128);
                     tc_mma(tmem + Lt::COL_P3, ad, bd, id_p3, (c > 0 || ks > 0));
                 }
-                // dG[chunk] = KR^T . (e o A3)   (M = 128 pairs, N = JP, K = 128 entries)
-                constexpr uint32_t id_dg = tc_idesc_bf16(128, JP, 1, 1);
+                // dG[chunk] = KR^T . (e o A3)   (M = 128 pairs, N = JK, K = 128 entries)
+                constexpr uint32_t id_dg = tc_idesc_bf16(128, JK, 1, 1);
 #pragma unroll
                 for (int ks = 0; ks < kBfTile / 16; ++ks) {
                     const uint64_t ad = tc_sdesc(sKR + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
@@ -284,16 +296,16 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             phase ^= 1;
             tc_fence_after();
             if (nb > 0) {
-                // lane tid holds pair kChunk*c + tid = j1 JP + j2 (inside the layout when
+                // lane tid holds pair kChunk*c + tid = j1 JQ + j2 (inside the layout when
                 // j1, j2 < jp, and then its j3 < ldg go out); the regulariser reads the BF16
                 // copy of G (its term, eta cs lambda / (W |Omega|) G, sits far below G's
                 // FP32 ulp)
                 const int pair = kChunk * c + tid;
-                const int j1 = pair / JP, j2 = pair % JP;
-                const bool inside = j1 < P.jp && j2 < P.jp;
+                const int j1 = pair / JQ, j2 = pair % JQ;
+                const bool inside = pair < NQ && j1 < P.jp && j2 < P.jp;
                 float* g = P.G + ((int64_t)j1 * P.jp + j2) * P.ldg;
 #pragma unroll
-                for (int h = 0; h < JP / 16; ++h) {
+                for (int h = 0; h < JK / 16; ++h) {
                     float d[16];
                     tmem_ld16(lane_base + Lt::COL_DG + 16 * h, d);
 #pragma unroll
@@ -302,7 +314,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                         float gv[4];
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            gv[i] = __bfloat162float(gbf[g_off<JP>(pair, 16 * h + 4 * q + i) / 2]);
+                            gv[i] = __bfloat162float(gbf[g_off<JK>(pair, 16 * h + 4 * q + i) / 2]);
                         red_add_v4(g + 16 * h + 4 * q, fmaf(sc, d[4 * q], -rg * gv[0]),
                                    fmaf(sc, d[4 * q + 1], -rg * gv[1]),
                                    fmaf(sc, d[4 * q + 2], -rg * gv[2]),
@@ -316,9 +328,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         }
         // ---- row gradients (Eq. (8)) into the tile's slots
         {
-            float p3[JP];
+            float p3[JK];
 #pragma unroll
-            for (int h = 0; h < JP / 16; ++h) {
+            for (int h = 0; h < JK / 16; ++h) {
                 float v[16];
                 tmem_ld16(lane_base + Lt::COL_P3 + 16 * h, v);
 #pragma unroll
@@ -330,17 +342,17 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 const float r2 = P.lambda_reg * inv[2];
                 float c[JPR];
 #pragma unroll
-                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p1[j], r0 * a1[j]);
+                for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p1[j], r0 * a1[j]);
                 put_slot<JPR>(smem, H, 0, tp[0], c);
 #pragma unroll
-                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p2[j], r1 * a2[j]);
+                for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p2[j], r1 * a2[j]);
                 put_slot<JPR>(smem, H, 1, tp[1], c);
 #pragma unroll
-                for (int j = 0; j < JP; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
+                for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
                 put_slot<JPR>(smem, H, 2, tp[2], c);
             }
         }
-        hog_coupled<JP>(P, Gr, t, smem, H, tid, kBfTile);
+        hog_coupled<JQ>(P, Gr, t, smem, H, tid, kBfTile);
         tc_fence_before();
         __syncthreads();
         hog_flush<JPR>(P, smem, H, eta, row_mean);
@@ -354,8 +366,11 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     if (warp == 0) tmem_dealloc(tmem, kTmemCols);
 }
 
+// JP: the rank the form computes at, 16, 20 or 32 (the slot rows hold JP floats)
 static size_t bf16_fixed_bytes(int JP) {
-    return JP == 16 ? BfLayout<16>::OFF_SLOTS : JP == 32 ? BfLayout<32>::OFF_SLOTS : 0;
+    return JP == 16 ? BfLayout<16, 16>::OFF_SLOTS
+         : JP == 20 ? BfLayout<20, 32>::OFF_SLOTS
+         : JP == 32 ? BfLayout<32, 32>::OFF_SLOTS : 0;
 }
 
 size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF) {
@@ -379,14 +394,14 @@ static cudaError_t prep_bf16(K kernel, size_t smem) {
     return e;
 }
 
-template <int JP>
+template <int JQ, int JK>
 static cudaError_t launch_bf16(const DParams& P, const DGroup& G, int64_t n_tiles, int* tile_counter,
                                int grid, const float* eta, int row_mean, float core_step_scale,
                                const HogSmem& H, size_t smem, int* err_flag, cudaStream_t s) {
-    cudaError_t e = prep_bf16(k_tensor_hog_bf16<JP>, smem);
+    cudaError_t e = prep_bf16(k_tensor_hog_bf16<JQ, JK>, smem);
     if (e != cudaSuccess) return e;
-    k_tensor_hog_bf16<JP><<<grid, kBfTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
-                                                      core_step_scale, H, err_flag);
+    k_tensor_hog_bf16<JQ, JK><<<grid, kBfTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
+                                                          core_step_scale, H, err_flag);
     return cudaGetLastError();
 }
 
@@ -402,10 +417,13 @@ cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, in
                   sizeof(float);
     if (smem < kBfMinSmem) smem = kBfMinSmem;
     if (JP == 16)
-        return launch_bf16<16>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
+        return launch_bf16<16, 16>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
+                                   H, smem, err_flag, s);
+    if (JP == 20)
+        return launch_bf16<20, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
+                                   H, smem, err_flag, s);
+    return launch_bf16<32, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
                                smem, err_flag, s);
-    return launch_bf16<32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
-                           smem, err_flag, s);
 }
 
 // CTAs of the BF16 kernel that fit on one SM with this much dynamic shared memory (at most
@@ -416,11 +434,14 @@ int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaErrorInvalidValue;
     if (JP == 16) {
-        e = prep_bf16(k_tensor_hog_bf16<16>, smem);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<16>);
+        e = prep_bf16(k_tensor_hog_bf16<16, 16>, smem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<16, 16>);
+    } else if (JP == 20) {
+        e = prep_bf16(k_tensor_hog_bf16<20, 32>, smem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<20, 32>);
     } else if (JP == 32) {
-        e = prep_bf16(k_tensor_hog_bf16<32>, smem);
-        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<32>);
+        e = prep_bf16(k_tensor_hog_bf16<32, 32>, smem);
+        if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<32, 32>);
     }
     if (e != cudaSuccess) return 0;
     int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0;
