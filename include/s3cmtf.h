@@ -100,7 +100,7 @@ typedef struct {
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by
                            gamma / kappa; every other row takes the plain lock-free step.
-                           0 = default 320 / (largest rank), i.e. 32 at rank 10 (a coupled
+                           0 = default 360 / (largest rank), i.e. 36 at rank 10 (a coupled
                            entry's step grows stiffer with the rank); < 0 disables the
                            scaling. */
     int hog_ctas;       /* HOGWILD: CTAs working at once (0 = default: on 3-way tensors, enough

@@ -561,13 +561,14 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // staleness-aware step: a row with kappa updates expected in flight at once takes
     // gamma / kappa of its step when kappa > gamma (kappa = occurrences x entries in flight
     // / |Omega|); each HOGWILD grouping stores the scale of every row.  Default gamma =
-    // 320 / (largest rank): 32 at rank 10.  A coupled entry's step has curvature
-    // eta * lambda_m * ||v||^2, which grows with the rank, and gamma stale steps of it must
-    // stay well inside the stable range.
+    // 360 / (largest rank): 36 at rank 10, where the HOGWILD test-RMSE curve sits closest to
+    // Algorithm 1's (larger gamma ends below it, smaller starts above it).  A coupled
+    // entry's step has curvature eta * lambda_m * ||v||^2, which grows with the rank, and
+    // gamma stale steps of it must stay well inside the stable range.
     {
         int jmax = 1;
         for (int n = 0; n < N; ++n) jmax = std::max(jmax, ctx->J[n]);
-        const double gamma = hp->hog_staleness == 0.f ? 320.0 / jmax : (double)hp->hog_staleness;
+        const double gamma = hp->hog_staleness == 0.f ? 360.0 / jmax : (double)hp->hog_staleness;
         auto row_scales = [&](DevGrouping& D, double inflight) -> int {
             for (int F = 0; F < nF; ++F) {
                 std::vector<float> d(occ[(size_t)F].size(), 1.f);

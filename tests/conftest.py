@@ -27,3 +27,11 @@ def cuda_lib():
         pytest.skip("no CUDA device")
     from paper_1708_08640_gb300 import _lib
     return _lib.load(build_if_missing=True)
+
+
+@pytest.fixture(scope="session")
+def rating_tensor():
+    """The cfg1 workload (3-way 100000 x 50000 x 1000 rating tensor, 10M entries, coupled
+    100000 x 100000 binary matrix), generated once per session."""
+    from paper_1708_08640_gb300 import synth
+    return synth.make_problem("cfg1")

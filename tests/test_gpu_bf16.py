@@ -82,11 +82,6 @@ def test_bf16_hogwild_single_tile_step(cuda_lib, J):
     assert max(errs.values()) < 3e-2, errs
 
 
-@pytest.fixture(scope="module")
-def rating_tensor():
-    return synth.make_problem("cfg1")
-
-
 @pytest.mark.parametrize("J", [16, 32])
 def test_bf16_rmse_tracks_fp32_on_rating_tensor(cuda_lib, rating_tensor, J):
     """cfg2 data at J = 16 and 32 (the cfg1 rating tensor): the BF16 form's test RMSE per

@@ -1,0 +1,72 @@
+"""The GPU epochs against the oracle's stored test-RMSE curves on the cfg1 workloads
+(tests/golden/curve_*.json, written by tests/golden/make_golden.py from oracle/ alone):
+the HOGWILD epoch tracks the sequential Algorithm 1 (P = 1) curve within 1% per epoch,
+and the deterministic minibatch epoch reproduces the oracle's minibatch curve."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_08640_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name, mode):
+    return json.load(open(os.path.join(GOLDEN, f"curve_{name}_{mode}.json")))
+
+
+def fingerprint(p):
+    """The stored curve's input fingerprint (the same hash make_golden.py records)."""
+    h = hashlib.sha256()
+    for a in (p.train_idx, p.train_val, p.test_idx, p.test_val):
+        h.update(np.ascontiguousarray(a).tobytes())
+    for c in p.coupled:
+        for a in (c.rows, c.cols, c.vals):
+            h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()[:16]
+
+
+def gpu_curve(p, rec, mode, **kw):
+    from paper_1708_08640_gb300.model import S3CMTF
+    hp = dict(rec["hparams"])
+    if rec.get("minibatch"):
+        mb = rec["minibatch"]
+        hp.update(batch=mb["batch"], core_scale=mb["core_scale"], row_rule="mean" if mb["row_mean"] else "sum")
+    m = S3CMTF.from_problem(p, order=synth.union_order(p, rec["order_seed"]), **hp, **kw)
+    m.set_params(*synth.init_params(p, rec["init_seed"]))
+    m.set_test(p.test_idx, p.test_val)
+    out = []
+    for _ in range(rec["epochs"]):
+        m.epoch(mode)
+        out.append(m.rmse())
+    m.close()
+    return np.array(out)
+
+
+def test_hogwild_tracks_algorithm1_on_cfg1(cuda_lib, rating_tensor):
+    """cfg1, J = 10, the default launch (29 184 tensor entries in flight): the HOGWILD
+    test RMSE after each of 10 epochs within 1% of Algorithm 1's (Section 3.3's lock-free
+    scheme against the sequential one, same data, start and visiting order)."""
+    rec = golden("cfg1", "sequential")
+    assert fingerprint(rating_tensor) == rec["fingerprint"]
+    got = gpu_curve(rating_tensor, rec, "hogwild")
+    ref = np.array(rec["test_rmse"])
+    dev = np.abs(got - ref) / ref
+    print("HOGWILD vs Algorithm 1, relative deviation per epoch:", np.round(dev, 5).tolist())
+    assert np.all(dev <= 0.01), dev
+
+
+def test_minibatch_reproduces_oracle_curve_on_cfg1(cuda_lib, rating_tensor):
+    """cfg1, J = 10: the deterministic minibatch epoch (B = 4096, row sum, core_scale 32)
+    against the oracle's FP64 curve of the same rule over 10 epochs."""
+    rec = golden("cfg1", "minibatch")
+    assert fingerprint(rating_tensor) == rec["fingerprint"]
+    got = gpu_curve(rating_tensor, rec, "minibatch")
+    ref = np.array(rec["test_rmse"])
+    dev = np.abs(got - ref) / ref
+    print("minibatch vs oracle, relative deviation per epoch:", np.round(dev, 8).tolist())
+    assert np.all(dev <= 1e-4), dev
