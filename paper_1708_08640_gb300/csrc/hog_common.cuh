@@ -68,16 +68,18 @@ __device__ __forceinline__ void load_row_ld(const float* __restrict__ p, int ld,
     }
 }
 
-// Eq. (8), coupled rows, for the coupled entries of tile t: read the current rows (P.ld
-// floats each, zero-extended to JP) and write the gradients to their slots (JP floats).
-// Threads first, first + stride, ... take the entries.
+// Eq. (8), coupled rows, for the coupled entries of a tile whose array ranges are in shared
+// memory (slo / shi, indexed as the lanes of hog_ranges: lane 1 + m holds matrix m): read the
+// current rows (P.ld floats each, zero-extended to JP) and write the gradients to their
+// slots (JP floats).  Threads first, first + stride, ... take the entries.
 template <int JP>
-__device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, int64_t t,
-                                            float* smem, const HogSmem& H, int first, int stride) {
+__device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, const int64_t* slo,
+                                            const int64_t* shi, float* smem, const HogSmem& H,
+                                            int first, int stride) {
     constexpr int JPR = round4(JP);
     for (int m = 0; m < P.M; ++m) {
         const int c = P.cmode[m];
-        const int64_t c0 = Gr.c_off[m][t], c1 = Gr.c_off[m][t + 1];
+        const int64_t c0 = slo[1 + m], c1 = shi[1 + m];
         const float lm = P.lambda_m;
         for (int64_t e = c0 + first; e < c1; e += stride) {
             const int32_t r = __ldg(Gr.cr[m] + e), k = __ldg(Gr.cc[m] + e);
@@ -101,23 +103,39 @@ __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, 
     }
 }
 
-// Tile t's segment table, per factor and segment: (row, first slot, events, step scale),
-// 16 bytes, in shared memory, with the segment counts; loaded in the tile's prologue so
-// that the flush needs no global round trip.  Threads first, first + stride, ... take part.
-// Ends without a barrier.
-__device__ __forceinline__ void hog_tables(const DGroup& Gr, int64_t t, float* smem,
-                                           const HogSmem& H, int first, int stride) {
+// A tile's segment table, per factor and segment: (row, first slot, events, step scale),
+// 16 bytes, in shared memory, with the segment counts, for a tile whose array ranges are in
+// shared memory (slo / shi, the lanes of hog_ranges).  hog_tables_async issues the first
+// three words as cp.async copies and stores the counts; once every thread has waited for its
+// copies (cp_async_wait_all) and a CTA barrier has passed, hog_tables_damp gathers each
+// segment's step scale (indexed by the segment's row) the same way; the flush reads the
+// table after a second wait and barrier.  No thread stalls on these loads: the table is
+// needed only by the flush, so its round trips overlap the tile's arithmetic.  Threads
+// first, first + stride, ... take part.
+__device__ __forceinline__ void hog_tables_async(const DParams& P, const DGroup& Gr,
+                                                 const int64_t* slo, const int64_t* shi, float* smem,
+                                                 const HogSmem& H, int first, int stride) {
     int* cnts = reinterpret_cast<int*>(smem + H.noff);
     for (int F = 0; F < H.nF; ++F) {
-        const int64_t s0 = Gr.seg_off[F][t];
-        const int ns = (int)(Gr.seg_off[F][t + 1] - s0);
+        const int64_t s0 = slo[1 + P.M + F];
+        const int ns = (int)(shi[1 + P.M + F] - s0);
         if (first == 0) cnts[F] = ns;
-        int4* tab = reinterpret_cast<int4*>(smem + H.toff[F]);
+        int* tab = reinterpret_cast<int*>(smem + H.toff[F]);
         for (int l = first; l < ns; l += stride) {
-            const int32_t row = __ldg(Gr.seg_row[F] + s0 + l);
-            tab[l] = make_int4(row, __ldg(Gr.seg_start[F] + s0 + l), __ldg(Gr.seg_cnt[F] + s0 + l),
-                               __float_as_int(__ldg(Gr.row_damp[F] + row)));
+            cp_async4(tab + 4 * l, Gr.seg_row[F] + s0 + l);
+            cp_async4(tab + 4 * l + 1, Gr.seg_start[F] + s0 + l);
+            cp_async4(tab + 4 * l + 2, Gr.seg_cnt[F] + s0 + l);
         }
+    }
+}
+
+__device__ __forceinline__ void hog_tables_damp(const DGroup& Gr, float* smem, const HogSmem& H,
+                                                int first, int stride) {
+    const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
+    for (int F = 0; F < H.nF; ++F) {
+        const int ns = cnts[F];
+        int* tab = reinterpret_cast<int*>(smem + H.toff[F]);
+        for (int l = first; l < ns; l += stride) cp_async4(tab + 4 * l + 3, Gr.row_damp[F] + tab[4 * l]);
     }
 }
 

@@ -32,20 +32,28 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
     extern __shared__ __align__(16) float smem[];
     __shared__ float s_lam[JPR];
     __shared__ float s_red[kCpThreads / 32][JPR];
-    __shared__ int s_tile;
+    __shared__ int64_t s_cur, s_nxt;        // this tile and the one claimed after it
+    __shared__ int64_t s_lo[32], s_hi[32];  // array ranges of this tile (hog_ranges lanes)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float eta = *eta_p;
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+    // tiles claimed two ahead, their ranges read one ahead (as in the BF16 Tucker kernel):
+    // the segment table goes out as asynchronous copies at the tile's start
+    if (tid == 0) {
+        s_cur = atomicAdd(tile_counter, 1);
+        s_nxt = atomicAdd(tile_counter, 1);
+    }
+    __syncthreads();
+    if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
     __syncthreads();
     for (;;) {
-        const int64_t t = s_tile;
+        const int64_t t = s_cur;
         if (t >= n_tiles) break;
-        int next = 0;
-        if (tid == 0) next = atomicAdd(tile_counter, 1);   // needed only at the tile's end
-        const int64_t e0 = Gr.t_off[t];
-        const int nb = (int)(Gr.t_off[t + 1] - e0);
+        int claim = 0;
+        if (tid == 0) claim = atomicAdd(tile_counter, 1);   // needed only at the tile's end
+        const int64_t e0 = s_lo[0];
+        const int nb = (int)(s_hi[0] - e0);
+        hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kCpThreads);
         if (tid < JP) s_lam[tid] = __ldcg(P.G + cp_diag(N, JP, P.ldg, tid));
-        hog_tables(Gr, t, smem, H, tid, kCpThreads);
         __syncthreads();
         float gd[JP];   // this entry's e * prod_n a_n, the diagonal's gradient (negated)
 #pragma unroll
@@ -92,7 +100,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
 #pragma unroll
             for (int j = 0; j < JP; ++j) gd[j] = err * prod[j];
         }
-        hog_coupled<JP>(P, Gr, t, smem, H, tid, kCpThreads);
+        hog_coupled<JP>(P, Gr, s_lo, s_hi, smem, H, tid, kCpThreads);
         // the tile's diagonal gradient: warp butterflies, then the warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1)
@@ -101,7 +109,9 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
         if (lane == 0)
 #pragma unroll
             for (int j = 0; j < JP; ++j) s_red[warp][j] = gd[j];
+        cp_async_wait_all();   // this thread's table copies
         __syncthreads();
+        hog_tables_damp(Gr, smem, H, tid, kCpThreads);
         // G_jj += eta cs / W (sum_b e_b prod_n a_n[j] / n_t - lambda_reg / |Omega| G_jj)
         if (tid < JP && nb > 0) {
             float s = 0.f;
@@ -110,8 +120,22 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
             const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
             atomicAdd(P.G + cp_diag(N, JP, P.ldg, tid), fmaf(sc, s, -rg * s_lam[tid]));
         }
+        cp_async_wait_all();   // this thread's step-scale copies
+        __syncthreads();
+        // the next tile's ranges are read while this one's row steps go out (nothing reads
+        // s_lo / s_hi / s_nxt past the barrier above until the one below)
+        int64_t lo = 0, hi = 0;
+        if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
         hog_flush<JPR>(P, smem, H, eta, row_mean);
-        if (tid == 0) s_tile = next;
+        __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
+        if (tid < 32) {
+            s_lo[tid] = lo;
+            s_hi[tid] = hi;
+        }
+        if (tid == 0) {
+            s_cur = s_nxt;
+            s_nxt = claim;
+        }
         __syncthreads();
     }
 }

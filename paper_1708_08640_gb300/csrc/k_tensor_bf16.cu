@@ -94,7 +94,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     float* smem = reinterpret_cast<float*>(smem_raw);
     __shared__ uint32_t s_tmem;
     __shared__ __align__(8) uint64_t s_mbar;
-    __shared__ int s_tile;
+    __shared__ int64_t s_cur, s_nxt;        // this tile and the one claimed after it
+    __shared__ int64_t s_lo[32], s_hi[32];  // array ranges of this tile (hog_ranges lanes)
     __shared__ int s_fail;   // set when a bounded wait ran out; read after barriers only
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t sbase = smem_u32(smem_raw);
@@ -119,15 +120,41 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
     uint32_t phase = 0;
 
-    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
+    // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
+    // starts with its ranges (entries, coupled entries, segments) in shared memory: its
+    // segment table goes out as asynchronous copies at once, and its critical path is the
+    // entries' index loads, then their rows.
+    if (tid == 0) {
+        s_cur = atomicAdd(tile_counter, 1);
+        s_nxt = atomicAdd(tile_counter, 1);
+    }
+    __syncthreads();
+    if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
     __syncthreads();
     for (;;) {
-        const int64_t t = s_tile;
+        const int64_t t = s_cur;
         if (t >= n_tiles || s_fail) break;
-        // the next tile is claimed now; its index is needed only at the end of this one
-        int next = 0;
-        if (tid == 0) next = atomicAdd(tile_counter, 1);
-        hog_tables(Gr, t, smem, H, tid, kBfTile);
+        // the tile after the next one is claimed now; it is needed only at this one's end
+        int claim = 0;
+        if (tid == 0) claim = atomicAdd(tile_counter, 1);
+        hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
+        // ---- this thread's entry: indices first, so that their round trip overlaps the
+        //      core's reload
+        const int64_t e0 = s_lo[0];
+        const int nb = (int)(s_hi[0] - e0);
+        const bool valid = tid < nb;
+        const int64_t e = e0 + tid;
+        int32_t row[3] = {0, 0, 0};
+        int32_t tp[3] = {0, 0, 0};
+        float x = 0.f;
+        if (valid) {
+#pragma unroll
+            for (int n = 0; n < 3; ++n) {
+                row[n] = __ldg(Gr.tidx[n] + e);
+                tp[n] = __ldg(Gr.tpos[n] + e);
+            }
+            x = __ldg(Gr.tval + e);
+        }
         // ---- the current core as BF16 operand: coalesced float4 reads of G (the layout's
         //      jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix
         //      layout (pair = j1 JQ + j2); the padding past jp stays zero
@@ -155,30 +182,15 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                         __float2bfloat16_rn(vv[i]);
             }
         }
-        // ---- this thread's entry
-        const int64_t e0 = Gr.t_off[t];
-        const int nb = (int)(Gr.t_off[t + 1] - e0);
-        const bool valid = tid < nb;
-        const int64_t e = e0 + tid;
+        // ---- the entry's rows, and the rows' 1 / |Omega^{n,i}| (used after the MMAs)
         float a1[JQ], a2[JQ], a3[JK];
-        float x = 0.f;
-        // the rows' 1 / |Omega^{n,i}| and the entry's slot positions, loaded with the rows
-        // (they are used after the MMAs)
         float inv[3] = {0.f, 0.f, 0.f};
-        int32_t tp[3] = {0, 0, 0};
         if (valid) {
-            int32_t row[3];
-#pragma unroll
-            for (int n = 0; n < 3; ++n) {
-                row[n] = __ldg(Gr.tidx[n] + e);
-                tp[n] = __ldg(Gr.tpos[n] + e);
-            }
             load_row_ld<JQ>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
             load_row_ld<JQ>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
             load_row_ld<JK>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
 #pragma unroll
             for (int n = 0; n < 3; ++n) inv[n] = __ldg(P.inv_cnt[n] + row[n]);
-            x = __ldg(Gr.tval + e);
         } else {
 #pragma unroll
             for (int j = 0; j < JQ; ++j) { a1[j] = 0.f; a2[j] = 0.f; }
@@ -231,10 +243,14 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     p2[j2] = fmaf(v[i], a1[j1], p2[j2]);
                 }
             }
-            // every lane has read T before the next chunk's MMA overwrites it
+            // every lane has read T before the next chunk's MMA overwrites it; after the
+            // last chunk, every thread's table copies have landed too
+            if (c == NC - 1) cp_async_wait_all();
             tc_fence_before();
             __syncthreads();
         }
+        // the segments' step scales, gathered by the rows the table copies brought
+        hog_tables_damp(Gr, smem, H, tid, kBfTile);
         float xt = 0.f;
 #pragma unroll
         for (int j = 0; j < JQ; ++j) xt = fmaf(a1[j], p1[j], xt);
@@ -352,11 +368,24 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 put_slot<JPR>(smem, H, 2, tp[2], c);
             }
         }
-        hog_coupled<JQ>(P, Gr, t, smem, H, tid, kBfTile);
+        hog_coupled<JQ>(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
+        cp_async_wait_all();
         tc_fence_before();
         __syncthreads();
+        // the next tile's ranges are read while this one's row steps go out (nothing reads
+        // s_lo / s_hi / s_nxt past the barrier above until the one below)
+        int64_t lo = 0, hi = 0;
+        if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
         hog_flush<JPR>(P, smem, H, eta, row_mean);
-        if (tid == 0) s_tile = next;
+        __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
+        if (tid < 32) {
+            s_lo[tid] = lo;
+            s_hi[tid] = hi;
+        }
+        if (tid == 0) {
+            s_cur = s_nxt;
+            s_nxt = claim;
+        }
         __syncthreads();
     }
     tc_fence_before();
