@@ -58,7 +58,7 @@ class _Params(C.Structure):
 class _HParams(C.Structure):
     _fields_ = [("lr0", C.c_double), ("mu", C.c_double), ("lambda_reg", C.c_double),
                 ("lambda_m", C.c_double), ("core_scale", C.c_double), ("batch", C.c_int64),
-                ("row_mean", C.c_int), ("cp", C.c_int)]
+                ("row_mean", C.c_int), ("cp", C.c_int), ("nonneg", C.c_int)]
 
 
 def _lib_handle():
@@ -144,7 +144,7 @@ class Oracle:
                        lambda_reg=hp.get("lambda_reg", 0.01),
                        lambda_m=hp.get("lambda_m", 1.0), core_scale=hp.get("core_scale", 1.0),
                        batch=int(hp.get("batch", 1)), row_mean=int(hp.get("row_mean", 0)),
-                       cp=int(hp.get("cp", 0)))
+                       cp=int(hp.get("cp", 0)), nonneg=int(hp.get("nonneg", 0)))
         self.G = np.zeros(self.J)
         self.U = [np.zeros((d, j)) for d, j in zip(self.dims, self.J)]
         self.V = [np.zeros((c.K, self.J[c.mode])) for c in cps]
@@ -172,7 +172,7 @@ class Oracle:
         h = dict(self.hp)
         h.update(over)
         return _HParams(h["lr0"], h["mu"], h["lambda_reg"], h["lambda_m"], h["core_scale"],
-                        int(h["batch"]), int(h["row_mean"]), int(h["cp"]))
+                        int(h["batch"]), int(h["row_mean"]), int(h["cp"]), int(h["nonneg"]))
 
     # -- O1
     def predict(self, idx):

@@ -28,6 +28,11 @@
  *   - eta_t = eta_0 / (1 + mu t) with t the 0-based epoch number.
  *   - S3CMTF-CP (cp = 1): the core is hyper-diagonal; its off-diagonal entries are not
  *     parameters, so every core step and the core gradient keep only the diagonal.
+ *   - non-negative form (nonneg = 1; Section 5 names the projected gradient method, Lin
+ *     2007, and gives no update rule): every SGD step of Alg. 1 or of the minibatch epoch
+ *     is followed by the projection max(0, .) of each parameter that the step changed
+ *     (the entry's rows, the core, the coupled entry's two rows); the full gradient is the
+ *     plain gradient of Eq. (7).
  *   - minibatch epoch (not in the paper): all gradients of a batch at the batch-start
  *     parameters; rows take eta * (sum of their gradients) [/ their count in the batch when
  *     row_mean is set]; the core takes eta * core_scale * (mean of its per-entry gradients
@@ -71,9 +76,18 @@ typedef struct {
     int cp;                      /* 1: S3CMTF-CP, the core is hyper-diagonal (Section 4.2,
                                     comparison with SALS): only its diagonal is a parameter,
                                     so core steps and the core gradient keep the diagonal */
+    int nonneg;                  /* 1: non-negative factorisation by projected SGD (Section 5,
+                                    "Discovery"): after every step, each parameter the step
+                                    changed is projected onto [0, inf), max(0, value) */
 } s3o_hparams;
 
 /* ------------------------------------------------------------------ small helpers */
+
+/* the projection onto the non-negative orthant, element by element */
+static void project_nonneg(double* v, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!(v[i] > 0.0)) v[i] = 0.0;
+}
 
 static int64_t core_size(int N, const int* J) {
     int64_t P = 1;
@@ -527,8 +541,10 @@ int s3o_epoch_sequential(const s3o_data* d, s3o_params* p, const s3o_hparams* hp
             for (int n = 0; n < N; ++n) {
                 double* u = p->U[n] + (int64_t)d->idx[(int64_t)n * d->nnz + b] * J[n];
                 for (int q = 0; q < J[n]; ++q) u[q] -= eta * eg[n][q];
+                if (hp->nonneg) project_nonneg(u, J[n]);
             }
             for (int64_t l = 0; l < P; ++l) p->G[l] -= eta * eG[l];
+            if (hp->nonneg) project_nonneg(p->G, P);
         } else {
             int c = d->cmode[m];
             int Jc = J[c];
@@ -538,6 +554,10 @@ int s3o_epoch_sequential(const s3o_data* d, s3o_params* p, const s3o_hparams* hp
             for (int q = 0; q < Jc; ++q) {
                 u[q] -= eta * gu[q];
                 v[q] -= eta * gv[q];
+            }
+            if (hp->nonneg) {
+                project_nonneg(u, Jc);
+                project_nonneg(v, Jc);
             }
         }
     }
@@ -633,6 +653,7 @@ int s3o_epoch_minibatch(const s3o_data* d, s3o_params* p, const s3o_hparams* hp,
                 double* u = p->U[f] + i * J[f];
                 double* D = DU[f] + i * J[f];
                 for (int q = 0; q < J[f]; ++q) { u[q] -= eta * D[q] / den; D[q] = 0.0; }
+                if (hp->nonneg) project_nonneg(u, J[f]);
                 hU[f][i] = 0;
             } else {
                 int m = f - N;
@@ -642,12 +663,14 @@ int s3o_epoch_minibatch(const s3o_data* d, s3o_params* p, const s3o_hparams* hp,
                 double* v = p->V[m] + i * Jc;
                 double* D = DV[m] + i * Jc;
                 for (int q = 0; q < Jc; ++q) { v[q] -= eta * D[q] / den; D[q] = 0.0; }
+                if (hp->nonneg) project_nonneg(v, Jc);
                 hV[m][i] = 0;
             }
         }
         if (nt > 0) {
             double w = eta * hp->core_scale / (double)nt;
             for (int64_t l = 0; l < P; ++l) { p->G[l] -= w * DG[l]; DG[l] = 0.0; }
+            if (hp->nonneg) project_nonneg(p->G, P);
         }
     }
     for (int n = 0; n < N; ++n) { free(DU[n]); free(hU[n]); free(eg[n]); }

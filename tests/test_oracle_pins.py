@@ -464,3 +464,117 @@ def test_cp_minibatch_keeps_the_core_hyperdiagonal():
     diag = G1[np.arange(J), np.arange(J), np.arange(J)].copy()
     G1[np.arange(J), np.arange(J), np.arange(J)] = 0.0
     assert np.all(G1 == 0.0) and np.all(diag != lam)
+
+
+# ------------------------------------------------------------------ non-negative form (Section 5)
+# Section 5 fits a non-negative factorisation with the projected gradient method (Lin
+# 2007): a gradient step followed by the projection onto the non-negative orthant,
+# max(0, .) element by element.  These pins tie the oracle's nonneg = 1 path to sympy
+# derivatives, to the pinned full gradient, and to the plain path where no projection binds.
+
+def test_nonneg_rank_one_step_by_symbolic_differentiation():
+    """J = 1: a tensor step that drives b below zero, then a coupled step that drives w
+    below zero; each step is the sympy gradient step followed by max(0, .)."""
+    sympy = pytest.importorskip("sympy")
+    g, a, b, c, w = sympy.symbols("g a b c w")
+    x, y, lam, lm, eta = -3.0, -2.0, 0.3, 2.0, 0.2
+    vals = {g: 0.9, a: 0.4, b: 0.05, c: 0.8, w: 0.2}
+    f_alpha = sympy.Rational(1, 2) * ((x - g * a * b * c) ** 2 + lam * g ** 2 + lam * (a ** 2 + b ** 2 + c ** 2))
+    f_beta = lm / 2 * ((y - a * w) ** 2 + lam * w ** 2)
+    raw1 = {s: float(vals[s] - eta * sympy.diff(f_alpha, s).subs(vals)) for s in (g, a, b, c)}
+    step1 = {s: max(0.0, v) for s, v in raw1.items()}
+    step1[w] = vals[w]
+    raw2 = {s: float(step1[s] - eta * sympy.diff(f_beta, s).subs(step1)) for s in (a, w)}
+    step2 = dict(step1)
+    step2.update({s: max(0.0, v) for s, v in raw2.items()})
+    # the example exercises both projections and leaves the other parameters inside
+    assert raw1[b] < 0 and raw2[w] < 0
+    assert min(raw1[g], raw1[a], raw1[c], raw2[a]) > 0
+    idx = np.zeros((3, 1), dtype=np.int32)
+    prob = Prob((1, 1, 1), (1, 1, 1), idx, np.array([x]),
+                [Cpl(0, 1, np.zeros(1, np.int32), np.zeros(1, np.int32), np.array([y]))])
+    o = make(prob, (np.array([[[0.9]]]), [np.array([[0.4]]), np.array([[0.05]]), np.array([[0.8]])],
+                    [np.array([[0.2]])]), lambda_reg=lam, lambda_m=lm, lr0=eta, mu=0.0, nonneg=1)
+    o.epoch_sequential(0, np.array([0, 1]))
+    G, U, V = o.get_params()
+    assert G.ravel()[0] == pytest.approx(step2[g], rel=1e-13)
+    assert U[0][0, 0] == pytest.approx(step2[a], rel=1e-13)
+    assert U[1][0, 0] == 0.0
+    assert U[2][0, 0] == pytest.approx(step2[c], rel=1e-13)
+    assert V[0][0, 0] == 0.0
+
+
+def test_nonneg_full_batch_is_a_projected_gradient_step():
+    """One batch holding every item: each touched row and the core take max(0, theta -
+    step * full gradient); rows no item touches keep their values."""
+    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=13,
+                                  coupled_nnz=20)
+    hp = dict(lr0=0.5, mu=0.0, lambda_reg=0.2, lambda_m=1.5, core_scale=2.0)
+    o = make(prob, params, nonneg=1, **hp)
+    gG, gU, gV = make(prob, params, **hp).full_gradient()
+    o.epoch_minibatch(0, np.arange(60), batch=60)
+    G, U, V = params
+    eG = np.maximum(0.0, G - 0.5 * 2.0 * gG / 40)
+    assert np.any(G - 0.5 * 2.0 * gG / 40 < 0) and np.any(eG > 0)
+    np.testing.assert_allclose(o.G, eG, rtol=1e-12, atol=1e-14)
+    c = prob.coupled[0]
+    clipped = 0
+    for n in range(3):
+        touched = np.zeros(prob.dims[n], bool)
+        touched[prob.train_idx[n]] = True
+        if n == c.mode:
+            touched[c.rows] = True
+        step = U[n] - 0.5 * gU[n]
+        clipped += int(np.sum(step[touched] < 0))
+        expect = np.where(touched[:, None], np.maximum(0.0, step), U[n])
+        np.testing.assert_allclose(o.U[n], expect, rtol=1e-12, atol=1e-14)
+    tv = np.zeros(c.K, bool)
+    tv[c.cols] = True
+    step = V[0] - 0.5 * gV[0]
+    clipped += int(np.sum(step[tv] < 0))
+    np.testing.assert_allclose(o.V[0], np.where(tv[:, None], np.maximum(0.0, step), V[0]),
+                               rtol=1e-12, atol=1e-14)
+    assert clipped > 0
+
+
+def test_nonneg_equals_plain_where_no_projection_binds():
+    """Non-negative parameters and values far above every prediction: each error is
+    positive, every step keeps the parameters non-negative, and the projected epochs
+    (sequential and minibatch) are the plain ones bit for bit."""
+    prob, (G, U, V) = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=15,
+                                     coupled_nnz=20)
+    rng = np.random.default_rng(3)
+    prob.train_val[:] = 30.0 + rng.random(prob.train_val.shape[0])
+    prob.coupled[0].vals[:] = 30.0 + rng.random(prob.coupled[0].vals.shape[0])
+    params = (np.abs(G), U, V)
+    hp = dict(lr0=0.002, mu=0.1, lambda_reg=0.2, lambda_m=1.5, core_scale=2.0, batch=16)
+    order = np.random.default_rng(4).permutation(60)
+    for epoch in ("epoch_sequential", "epoch_minibatch"):
+        a = make(prob, params, **hp)
+        b = make(prob, params, nonneg=1, **hp)
+        for t in range(3):
+            getattr(a, epoch)(t, order)
+            getattr(b, epoch)(t, order)
+        for x, y in zip([a.G] + a.U + a.V, [b.G] + b.U + b.V):
+            assert np.array_equal(x, y)
+        assert all(np.all(x >= 0) for x in [a.G] + a.U + a.V)
+
+
+def test_nonneg_minibatch_of_one_is_sequential():
+    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=16,
+                                  coupled_nnz=20)
+    order = np.random.default_rng(0).permutation(60)
+    hp = dict(lr0=0.1, mu=0.1, lambda_reg=0.2, lambda_m=1.5, nonneg=1)
+    a = make(prob, params, **hp)
+    b = make(prob, params, batch=1, **hp)
+    for t in range(2):
+        a.epoch_sequential(t, order)
+        b.epoch_minibatch(t, order)
+    for x, y in zip([a.G] + a.U + a.V, [b.G] + b.U + b.V):
+        np.testing.assert_allclose(x, y, rtol=1e-13, atol=1e-14)
+    assert all(np.all(x >= 0) for x in [a.G] + a.U + a.V)
+    # the projection binds on this example: the plain epochs leave negative parameters
+    c = make(prob, params, **{k: v for k, v in hp.items() if k != "nonneg"})
+    for t in range(2):
+        c.epoch_sequential(t, order)
+    assert np.any(c.G < 0) and np.any(c.V[0] < 0) and np.any(a.V[0] == 0)
