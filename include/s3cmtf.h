@@ -114,6 +114,16 @@ typedef struct {
                            are parameters (every mode needs the same rank); core steps and the
                            core gradient keep the diagonal, s3_set_params zeroes the rest, and
                            the HOGWILD epoch runs an O(N J) per-entry kernel.  FP32 form. */
+    int nonneg;         /* 1: non-negative factorisation by projected SGD (Section 5,
+                           "Discovery", which fits it with the projected gradient method): every
+                           step of either mode is followed by max(0, .) on each parameter it
+                           changed (rows, core).  HOGWILD applies the projection with an
+                           atomic max after each atomic add, so the last operation on every
+                           touched value is a projection.  A step whose result is NaN is
+                           projected to 0 (minibatch) or kept, if its sign bit is clear
+                           (HOGWILD).  Both precisions, and S3CMTF-CP.  The initial core may
+                           hold negative entries until its first step; the factors start
+                           non-negative (U(0,1)).  0 = the plain method. */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.

@@ -43,7 +43,7 @@ class s3_hparams(C.Structure):
     _fields_ = [("lr0", C.c_float), ("mu", C.c_float), ("lambda_reg", C.c_float),
                 ("lambda_m", C.c_float), ("batch", C.c_int), ("core_scale", C.c_float),
                 ("row_rule", C.c_int), ("hog_tile", C.c_int), ("hog_staleness", C.c_float),
-                ("hog_ctas", C.c_int), ("mb_ctas", C.c_int), ("cp", C.c_int)]
+                ("hog_ctas", C.c_int), ("mb_ctas", C.c_int), ("cp", C.c_int), ("nonneg", C.c_int)]
 
 
 class S3Error(RuntimeError):

@@ -232,6 +232,7 @@ static void fill_params(s3_ctx* ctx) {
     P.ldg = ctx->JPR;
     P.jp = ctx->JP;
     P.cp = ctx->hp.cp;
+    P.nonneg = ctx->hp.nonneg;
     for (int m = 0; m < ctx->M; ++m) P.cmode[m] = ctx->cmode[m];
     for (int F = 0; F < ctx->N + ctx->M; ++F) P.inv_cnt[F] = ctx->inv_cnt[F];
     P.lambda_reg = ctx->hp.lambda_reg;
@@ -313,7 +314,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
             if (J[n] != J[0]) return bail(S3_ERR_ARG, "S3CMTF-CP (hp.cp = 1) needs equal ranks in every mode");
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
-        hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0 || (hp->cp != 0 && hp->cp != 1))
+        hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0 || (hp->cp != 0 && hp->cp != 1) ||
+        (hp->nonneg != 0 && hp->nonneg != 1))
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];

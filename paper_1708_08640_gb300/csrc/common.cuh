@@ -23,6 +23,7 @@ struct DParams {
     int ldg;                       // row stride (floats) of the padded core's last mode
     int jp;                        // padded rank: the core is jp x .. x jp x ldg
     int cp;                        // 1: S3CMTF-CP, the core is hyper-diagonal
+    int nonneg;                    // 1: every step is followed by max(0, .) (projected SGD)
     int N, M;
     int cmode[kMaxM];
     float lambda_reg, lambda_m, inv_nnz;
@@ -86,6 +87,31 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};"
                  :: "l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// max(0, v) of the non-negative form, for values one thread owns; a NaN becomes 0
+__device__ __forceinline__ float project(float v) { return v > 0.f ? v : 0.f; }
+__device__ __forceinline__ void project4(float4& u) {
+    u.x = project(u.x);
+    u.y = project(u.y);
+    u.z = project(u.z);
+    u.w = project(u.w);
+}
+
+// The projection max(0, v) of 4 consecutive floats in global memory that other threads may
+// be adding to: an atomic max of each value's bit pattern, read as a signed integer, with 0.
+// A float with its sign bit clear is a non-negative integer and keeps its value; one with it
+// set (negative, -0, or a NaN with the sign bit set) is a negative integer and becomes +0.
+// Issued by the thread that has just added to the same values, after its add (one thread's
+// operations on one address take effect in program order), so the last operation on every
+// touched value is a projection.
+__device__ __forceinline__ void red_proj_v4(float* p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        asm volatile("red.global.max.s32 [%0], %1;" :: "l"(p + i), "r"(0) : "memory");
+}
+__device__ __forceinline__ void red_proj(float* p) {
+    asm volatile("red.global.max.s32 [%0], %1;" :: "l"(p), "r"(0) : "memory");
 }
 
 // Neumaier-compensated FP32 accumulation.

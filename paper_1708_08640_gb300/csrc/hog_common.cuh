@@ -191,7 +191,9 @@ __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, c
                 acc.w += v.w;
             }
             const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
-            red_add_v4(base + (int64_t)rr * P.ld + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+            float* dst = base + (int64_t)rr * P.ld + 4 * q;
+            red_add_v4(dst, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+            if (P.nonneg) red_proj_v4(dst);
         }
     }
 }
@@ -315,7 +317,9 @@ __device__ __forceinline__ void hog_flush_meta(const DParams& P, const float* sm
             acc.w += v.w;
         }
         const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
-        red_add_v4(base + (int64_t)rr * JPR + 4 * q, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+        float* dst = base + (int64_t)rr * JPR + 4 * q;
+        red_add_v4(dst, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+        if (P.nonneg) red_proj_v4(dst);
     }
 }
 

@@ -118,7 +118,9 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
             for (int w = 0; w < kCpThreads / 32; ++w) s += s_red[w][tid];
             const float sc = eta * core_step_scale / (float)nb;
             const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
-            atomicAdd(P.G + cp_diag(N, JP, P.ldg, tid), fmaf(sc, s, -rg * s_lam[tid]));
+            float* gd = P.G + cp_diag(N, JP, P.ldg, tid);
+            atomicAdd(gd, fmaf(sc, s, -rg * s_lam[tid]));
+            if (P.nonneg) red_proj(gd);
         }
         cp_async_wait_all();   // this thread's step-scale copies
         __syncthreads();

@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                 u.y = fmaf(sc, k[4 * q + 1].value(), u.y);
                 u.z = fmaf(sc, k[4 * q + 2].value(), u.z);
                 u.w = fmaf(sc, k[4 * q + 3].value(), u.w);
+                if (P.nonneg) project4(u);
                 st4(base + 4 * q, u);
             }
         }
@@ -317,6 +318,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                     u.y = fmaf(sc, d.y, u.y);
                     u.z = fmaf(sc, d.z, u.z);
                     u.w = fmaf(sc, d.w, u.w);
+                    if (P.nonneg) project4(u);
                     st4(base, u);
                 }
             } else {
@@ -349,8 +351,9 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                 if (lane == 0 && ntb > 0 && core_elem) {
                     float* g = P.G + (l / JP) * JPR + (l % JP);
                     const float gv = *g;
-                    *g = gv + eta * A.core_scale * (sum / (float)ntb) -
-                         eta * A.core_scale * P.lambda_reg * P.inv_nnz * gv;
+                    const float nv = gv + eta * A.core_scale * (sum / (float)ntb) -
+                                     eta * A.core_scale * P.lambda_reg * P.inv_nnz * gv;
+                    *g = P.nonneg ? project(nv) : nv;
                 }
             }
         }

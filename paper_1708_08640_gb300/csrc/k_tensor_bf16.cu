@@ -335,6 +335,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                                    fmaf(sc, d[4 * q + 1], -rg * gv[1]),
                                    fmaf(sc, d[4 * q + 2], -rg * gv[2]),
                                    fmaf(sc, d[4 * q + 3], -rg * gv[3]));
+                        if (P.nonneg) red_proj_v4(g + 16 * h + 4 * q);
                     }
                 }
             }

@@ -387,9 +387,10 @@ struct CoreTile {
     }
 
     // G[q] += sc * tile - rg * G[q] for both multi-indices of pair p (the second only when it
-    // exists: JP odd pads the pair)
+    // exists: JP odd pads the pair); nonneg: each add is followed by the projection
     __device__ __forceinline__ static void add(float* G, const float* __restrict__ sG, int p,
-                                               const float (&tile)[2][JP], float sc, float rg) {
+                                               const float (&tile)[2][JP], float sc, float rg,
+                                               int nonneg) {
         const int q0 = (p / JH2) * JP + 2 * (p % JH2);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -401,15 +402,17 @@ struct CoreTile {
 #pragma unroll
             for (int j = 0; j < JPR; ++j) d[j] = j < JP ? fmaf(sc, tile[h][j], -rg * g[j]) : 0.f;
 #pragma unroll
-            for (int c = 0; c < JPR / 4; ++c)
+            for (int c = 0; c < JPR / 4; ++c) {
                 red_add_v4(G + q * JPR + 4 * c, d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+                if (nonneg) red_proj_v4(G + q * JPR + 4 * c);
+            }
         }
     }
 
     // Every one of the T threads calls apply (with several slices it has CTA barriers over
     // T threads, and the stage is overwritten).
     __device__ __forceinline__ static void apply(float* stage, int nb, const float* __restrict__ sG,
-                                                 float* G, float sc, float rg) {
+                                                 float* G, float sc, float rg, int nonneg) {
         const int t = threadIdx.x;
         if constexpr (KS > 1) {
             // (every thread reaches each barrier at the same instruction: warps can straddle
@@ -444,6 +447,7 @@ struct CoreTile {
                 const float4 g = *reinterpret_cast<const float4*>(sG + q * JPR + 4 * c);
                 red_add_v4(G + q * JPR + 4 * c, fmaf(sc, acc.x, -rg * g.x), fmaf(sc, acc.y, -rg * g.y),
                            fmaf(sc, acc.z, -rg * g.z), fmaf(sc, acc.w, -rg * g.w));
+                if (nonneg) red_proj_v4(G + q * JPR + 4 * c);
             }
         } else {
 #pragma unroll
@@ -452,7 +456,7 @@ struct CoreTile {
                 if (p >= QP) continue;
                 float tile[2][JP];
                 accumulate(stage, nb, p, 0, tile);
-                add(G, sG, p, tile, sc, rg);
+                add(G, sG, p, tile, sc, rg, nonneg);
             }
         }
     }

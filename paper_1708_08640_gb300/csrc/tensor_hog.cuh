@@ -263,7 +263,7 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
             if (nb > 0) {
                 const float sc = eta * core_step_scale / (float)nb;
                 const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
-                CoreTile<N, JP, ST, kT>::apply(stage, nb, sG, P.G, sc, rg);
+                CoreTile<N, JP, ST, kT>::apply(stage, nb, sG, P.G, sc, rg, P.nonneg);
             }
         }
         tile_barrier<kT>();

@@ -40,7 +40,8 @@ class S3CMTF:
 
     def __init__(self, dims, J, train_idx, train_val, coupled=(), *, lr0=0.01, mu=0.1,
                  lambda_reg=0.01, lambda_m=1.0, batch=4096, core_scale=1.0, row_rule="sum",
-                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, cp=0, seed=0, order=None,
+                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, cp=0, nonneg=0, seed=0,
+                 order=None,
                  device=None,
                  stream=None):
         self.lib = L.load()
@@ -73,7 +74,7 @@ class S3CMTF:
         hp = L.s3_hparams(lr0, mu, lambda_reg, lambda_m, int(batch), core_scale,
                           _ROW[row_rule] if isinstance(row_rule, str) else int(row_rule),
                           int(hog_tile), float(hog_staleness), int(hog_ctas), int(mb_ctas),
-                          int(cp))
+                          int(cp), int(nonneg))
         Jarr = (C.c_int * self.N)(*self.J)
         order_arr = None if order is None else _host(order, np.int64)
         with torch.cuda.device(self.device):

@@ -38,7 +38,7 @@ def make_pair(p, init_seed=1, order_seed=2, **hp):
     gpu.set_params(*params)
     orc = oracle.Oracle(q, **{k: v for k, v in h.items()
                              if k in ("lr0", "mu", "lambda_reg", "lambda_m", "batch",
-                                      "core_scale", "cp")},
+                                      "core_scale", "cp", "nonneg")},
                         row_mean=1 if h.get("row_rule", "sum") == "mean" else 0)
     orc.set_params(*params)
     return gpu, orc, q, order
