@@ -116,6 +116,10 @@ def test_rejects_bad_hparams(lib):
     assert _init(lib, idx, val, (5, 4, 3), (2, 2, 2), hp=h)[0] == L.S3_ERR_ARG
     h = L.s3_hparams(0.01, 0.1, 0.01, 1.0, 0, 1.0, 0, 0, 0.0, 0)
     assert _init(lib, idx, val, (5, 4, 3), (2, 2, 2), hp=h)[0] == L.S3_ERR_ARG
+    # the non-negative form is a flag: 0 or 1
+    h = L.s3_hparams(0.01, 0.1, 0.01, 1.0, 64, 1.0, 0, 0, 0.0, 0, 0, 0, 2)
+    st, msg = _init(lib, idx, val, (5, 4, 3), (2, 2, 2), hp=h)
+    assert st == L.S3_ERR_ARG and "hyper-parameters" in msg
 
 
 @pytest.mark.skipif(gpu_available(), reason="checks the no-device path")
