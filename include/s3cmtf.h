@@ -166,6 +166,7 @@ int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_matrix* Y, in
  *              operands and FP32 accumulation; FP32 master parameters and errors; HOGWILD
  *              mode, 3-way tensors, ranks up to 32, computed at rank 16, 20 or 32 (the
  *              last mode padded to 32 at rank 20) with zero padding; else S3_ERR_ARG).
+ * With hp.nonneg = 1 every step of either mode is a projected step (see s3_hparams).
  * Returns S3_ERR_DIVERGED if a non-finite parameter appeared (the parameters are left as
  * they are).  Enqueues work and synchronises once at the end to read the flag. */
 int s3_epoch(s3_ctx* ctx, int mode, int precision);
