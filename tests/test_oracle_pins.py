@@ -386,12 +386,16 @@ def _cp_problem(seed=11, J=3):
     return prob, (G, U, V), lam
 
 
-def test_cp_sequential_epoch_follows_the_cp_formulas():
+@pytest.mark.parametrize("nonneg", [0, 1])
+def test_cp_sequential_epoch_follows_the_cp_formulas(nonneg):
     """S3CMTF-CP (hyper-diagonal core, Section 4.2): Algorithm 1 with the CP model written
     out directly in numpy: x~ = sum_j l_j prod_n a_n[j]; du_n = -e l o prod_{m!=n} a_m +
-    (lambda_reg / c_n) a_n; dl = -e prod_n a_n + (lambda_reg / |Omega|) l; coupled as Eq. (8)."""
+    (lambda_reg / c_n) a_n; dl = -e prod_n a_n + (lambda_reg / |Omega|) l; coupled as Eq. (8).
+    nonneg = 1: each updated row and the diagonal then take max(0, .) (Section 5)."""
     prob, params, lam = _cp_problem()
-    hp = dict(lr0=0.05, mu=0.0, lambda_reg=0.3, lambda_m=1.5, cp=1)
+    hp = dict(lr0=0.05, mu=0.0, lambda_reg=0.3, lambda_m=1.5, cp=1, nonneg=nonneg)
+    proj = (lambda v: np.maximum(0.0, v)) if nonneg else (lambda v: v)
+    clipped = 0
     o = make(prob, params, **hp)
     n_union = prob.train_val.shape[0] + prob.coupled[0].rows.shape[0]
     order = np.random.default_rng(5).permutation(n_union)
@@ -414,14 +418,21 @@ def test_cp_sequential_epoch_follows_the_cp_formulas():
             e = x[it] - np.sum(lam * a[0] * a[1] * a[2])
             for n in range(3):
                 others = np.prod([a[m] for m in range(3) if m != n], axis=0)
-                U[n][idx[n, it]] -= eta * (-e * lam * others + lr / cnt[n][idx[n, it]] * a[n])
-            lam = lam - eta * (-e * a[0] * a[1] * a[2] + lr / nnz * lam)
+                step = U[n][idx[n, it]] - eta * (-e * lam * others + lr / cnt[n][idx[n, it]] * a[n])
+                clipped += int(np.sum(step < 0))
+                U[n][idx[n, it]] = proj(step)
+            step = lam - eta * (-e * a[0] * a[1] * a[2] + lr / nnz * lam)
+            clipped += int(np.sum(step < 0))
+            lam = proj(step)
         else:
             b = it - nnz
             u, v = U[c.mode][c.rows[b]].copy(), V[0][c.cols[b]].copy()
             e = c.vals[b] - u @ v
-            U[c.mode][c.rows[b]] -= eta * (-lm * e * v)
-            V[0][c.cols[b]] -= eta * (-lm * e * u + lm * lr / cntY[c.cols[b]] * v)
+            su = U[c.mode][c.rows[b]] - eta * (-lm * e * v)
+            sv = V[0][c.cols[b]] - eta * (-lm * e * u + lm * lr / cntY[c.cols[b]] * v)
+            clipped += int(np.sum(su < 0) + np.sum(sv < 0))
+            U[c.mode][c.rows[b]] = proj(su)
+            V[0][c.cols[b]] = proj(sv)
     J = lam.shape[0]
     np.testing.assert_allclose(G1[np.arange(J), np.arange(J), np.arange(J)], lam, rtol=1e-12, atol=1e-14)
     off = G1.copy()
@@ -430,6 +441,8 @@ def test_cp_sequential_epoch_follows_the_cp_formulas():
     for n in range(3):
         np.testing.assert_allclose(U1[n], U[n], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(V1[0], V[0], rtol=1e-12, atol=1e-14)
+    if nonneg:
+        assert clipped > 0 and min(G1.min(), V1[0].min(), *(u.min() for u in U1)) >= 0.0
 
 
 def test_cp_full_gradient_is_the_diagonal_of_central_differences():
@@ -504,36 +517,39 @@ def test_nonneg_rank_one_step_by_symbolic_differentiation():
     assert V[0][0, 0] == 0.0
 
 
-def test_nonneg_full_batch_is_a_projected_gradient_step():
+@pytest.mark.parametrize("dims,J,ncpl", [((6, 5, 4), (2, 3, 2), 1), ((5, 4, 3, 3), (2, 2, 3, 2), 2)])
+def test_nonneg_full_batch_is_a_projected_gradient_step(dims, J, ncpl):
     """One batch holding every item: each touched row and the core take max(0, theta -
-    step * full gradient); rows no item touches keep their values."""
-    prob, params = random_problem((6, 5, 4), (2, 3, 2), nnz=40, n_coupled=1, seed=13,
-                                  coupled_nnz=20)
+    step * full gradient); rows no item touches keep their values (3-way with one coupled
+    matrix, 4-way with two)."""
+    prob, params = random_problem(dims, J, nnz=40, n_coupled=ncpl, seed=13, coupled_nnz=20)
+    n_union = 40 + 20 * ncpl
     hp = dict(lr0=0.5, mu=0.0, lambda_reg=0.2, lambda_m=1.5, core_scale=2.0)
     o = make(prob, params, nonneg=1, **hp)
     gG, gU, gV = make(prob, params, **hp).full_gradient()
-    o.epoch_minibatch(0, np.arange(60), batch=60)
+    o.epoch_minibatch(0, np.arange(n_union), batch=n_union)
     G, U, V = params
     eG = np.maximum(0.0, G - 0.5 * 2.0 * gG / 40)
     assert np.any(G - 0.5 * 2.0 * gG / 40 < 0) and np.any(eG > 0)
     np.testing.assert_allclose(o.G, eG, rtol=1e-12, atol=1e-14)
-    c = prob.coupled[0]
     clipped = 0
-    for n in range(3):
+    for n in range(len(dims)):
         touched = np.zeros(prob.dims[n], bool)
         touched[prob.train_idx[n]] = True
-        if n == c.mode:
-            touched[c.rows] = True
+        for c in prob.coupled:
+            if n == c.mode:
+                touched[c.rows] = True
         step = U[n] - 0.5 * gU[n]
         clipped += int(np.sum(step[touched] < 0))
         expect = np.where(touched[:, None], np.maximum(0.0, step), U[n])
         np.testing.assert_allclose(o.U[n], expect, rtol=1e-12, atol=1e-14)
-    tv = np.zeros(c.K, bool)
-    tv[c.cols] = True
-    step = V[0] - 0.5 * gV[0]
-    clipped += int(np.sum(step[tv] < 0))
-    np.testing.assert_allclose(o.V[0], np.where(tv[:, None], np.maximum(0.0, step), V[0]),
-                               rtol=1e-12, atol=1e-14)
+    for m, c in enumerate(prob.coupled):
+        tv = np.zeros(c.K, bool)
+        tv[c.cols] = True
+        step = V[m] - 0.5 * gV[m]
+        clipped += int(np.sum(step[tv] < 0))
+        np.testing.assert_allclose(o.V[m], np.where(tv[:, None], np.maximum(0.0, step), V[m]),
+                                   rtol=1e-12, atol=1e-14)
     assert clipped > 0
 
 
