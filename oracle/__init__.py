@@ -83,6 +83,7 @@ def _lib_handle():
             lib.s3o_entry_gradient_opt.argtypes = [D, P, H, C.c_int64, dp, dp]
             lib.s3o_entry_gradient_opt.restype = C.c_double
             lib.s3o_full_gradient.argtypes = [D, P, H, dp, C.POINTER(dp), C.POINTER(dp)]
+            lib.s3o_full_gradient_w.argtypes = [D, P, H, dp, dp, C.POINTER(dp), C.POINTER(dp)]
             lib.s3o_learning_rate.argtypes = [H, C.c_int64]
             lib.s3o_learning_rate.restype = C.c_double
             lib.s3o_epoch_sequential.argtypes = [D, P, H, C.c_int64, lp, C.c_int64]
@@ -243,14 +244,24 @@ class Oracle:
     def entry_gradient_opt(self, e, **over):
         return self._entry_grad(self.lib.s3o_entry_gradient_opt, e, **over)
 
-    def full_gradient(self, **over):
+    def full_gradient(self, w=None, **over):
+        """Eq. (8) summed over every entry.  w: None, or one weight per train entry that
+        takes the place of -(x - x~) in the entry's data terms."""
         gG = np.empty(self.J)
         gU = [np.empty((d, j)) for d, j in zip(self.dims, self.J)]
         gV = [np.empty((c.K, self.J[c.mode])) for c in self.coupled]
         h = self._h(**over)
-        self.lib.s3o_full_gradient(C.byref(self.data), C.byref(self.params_c), C.byref(h),
-                                   _ptr(gG, C.c_double), _ptr_array(gU, C.c_double),
-                                   _ptr_array(gV, C.c_double))
+        if w is None:
+            self.lib.s3o_full_gradient(C.byref(self.data), C.byref(self.params_c), C.byref(h),
+                                       _ptr(gG, C.c_double), _ptr_array(gU, C.c_double),
+                                       _ptr_array(gV, C.c_double))
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            if w.shape != (self._x.shape[0],):
+                raise ValueError("w needs one weight per train entry")
+            self.lib.s3o_full_gradient_w(C.byref(self.data), C.byref(self.params_c), C.byref(h),
+                                         _ptr(w, C.c_double), _ptr(gG, C.c_double),
+                                         _ptr_array(gU, C.c_double), _ptr_array(gV, C.c_double))
         return gG, gU, gV
 
     # -- O4 / O5

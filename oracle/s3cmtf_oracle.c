@@ -443,9 +443,13 @@ double s3o_entry_gradient_opt(const s3o_data* d, const s3o_params* p, const s3o_
 }
 
 /* full gradient of f = sum over train entries and coupled entries of Eq. (8).
-   Outputs have the parameter shapes and are overwritten. */
-void s3o_full_gradient(const s3o_data* d, const s3o_params* p, const s3o_hparams* hp,
-                       double* gG, double* const* gU, double* const* gV) {
+   Outputs have the parameter shapes and are overwritten.
+   w: NULL, or one weight per train entry that takes the place of -(x - x~) in that entry's
+   data terms of Eq. (8) (so that a caller's upstream derivative with respect to the
+   prediction x~_alpha can be propagated); the regularisation and coupled-matrix terms are
+   those of Eq. (8) either way. */
+void s3o_full_gradient_w(const s3o_data* d, const s3o_params* p, const s3o_hparams* hp,
+                         const double* w, double* gG, double* const* gU, double* const* gV) {
     int N = d->N;
     const int* J = d->J;
     int64_t P = core_size(N, J);
@@ -458,7 +462,20 @@ void s3o_full_gradient(const s3o_data* d, const s3o_params* p, const s3o_hparams
     for (int n = 0; n < N; ++n) eg[n] = (double*)malloc(sizeof(double) * J[n]);
     double* eG = (double*)malloc(sizeof(double) * P);
     for (int64_t e = 0; e < d->nnz; ++e) {
-        compute_gradient(d, p, e, eg, eG);
+        double err = compute_gradient(d, p, e, eg, eG);
+        if (w) {
+            /* the data terms are -err times the partials and the outer product; rebuild them
+               with the weight in place of -err */
+            const double* a[8];
+            entry_rows(d, p, e, a);
+            for (int n = 0; n < N; ++n) {
+                partial_except(N, J, p->G, a, n, eg[n]);
+                for (int k = 0; k < J[n]; ++k) eg[n][k] *= w[e];
+            }
+            outer_rows(N, J, a, eG);
+            for (int64_t l = 0; l < P; ++l) eG[l] *= w[e];
+        }
+        (void)err;
         add_tensor_reg(d, p, e, cnt, hp->lambda_reg, eg, eG);
         for (int n = 0; n < N; ++n) {
             int64_t i = d->idx[(int64_t)n * d->nnz + e];
@@ -486,6 +503,11 @@ void s3o_full_gradient(const s3o_data* d, const s3o_params* p, const s3o_hparams
     free(eG);
     free_counts(cnt, N);
     free_counts(cntY, d->M);
+}
+
+void s3o_full_gradient(const s3o_data* d, const s3o_params* p, const s3o_hparams* hp,
+                       double* gG, double* const* gU, double* const* gV) {
+    s3o_full_gradient_w(d, p, hp, NULL, gG, gU, gV);
 }
 
 /* ------------------------------------------------------------------ exported: O4, O5 */

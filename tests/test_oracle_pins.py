@@ -163,6 +163,54 @@ def test_full_gradient_central_differences(dims, J, ncpl):
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-7), (kind, k, pos)
 
 
+@pytest.mark.parametrize("dims,J,ncpl", [((6, 5, 4), (2, 3, 2), 1), ((5, 4, 3, 3), (2, 2, 3, 2), 2)])
+def test_weighted_gradient_central_differences(dims, J, ncpl):
+    """Per-entry weights w in place of -e: the gradient of
+    F = sum_alpha w_alpha x~_alpha + (f - 1/2 sum_alpha e_alpha^2), i.e. the data term made
+    linear in the predictions with the regularisers and coupled terms of Eq. (7) kept; F is
+    evaluated from the pinned prediction and loss routines.  With w = -e it is the gradient
+    of f itself."""
+    prob, params = random_problem(dims, J, nnz=35, n_coupled=ncpl, seed=18, coupled_nnz=15)
+    hp = dict(lambda_reg=0.3, lambda_m=1.3)
+    o = make(prob, params, **hp)
+    rng = np.random.default_rng(5)
+    w = rng.normal(size=prob.train_val.shape[0])
+    gG, gU, gV = o.full_gradient(w=w)
+    G, U, V = params
+    idx, x = prob.train_idx.astype(np.int32), prob.train_val
+
+    def F_at(G_, U_, V_):
+        o.set_params(G_, U_, V_)
+        xt = o.predict(idx)
+        return float(np.dot(w, xt) + o.loss()[0] - 0.5 * np.sum((x - xt) ** 2))
+
+    checks = [("G", None, np.unravel_index(l, G.shape))
+              for l in rng.choice(G.size, size=min(G.size, 8), replace=False)]
+    for n in range(len(dims)):
+        for _ in range(5):
+            checks.append(("U", n, (rng.integers(dims[n]), rng.integers(J[n]))))
+    for m in range(ncpl):
+        for _ in range(5):
+            checks.append(("V", m, (rng.integers(V[m].shape[0]), rng.integers(V[m].shape[1]))))
+    for kind, k, pos in checks:
+        Gp, Up, Vp = G.copy(), [u.copy() for u in U], [v.copy() for v in V]
+        Gm, Um, Vm = G.copy(), [u.copy() for u in U], [v.copy() for v in V]
+        tgt_p = Gp if kind == "G" else (Up[k] if kind == "U" else Vp[k])
+        tgt_m = Gm if kind == "G" else (Um[k] if kind == "U" else Vm[k])
+        h = 1e-6 * max(1.0, abs(tgt_p[pos]))
+        tgt_p[pos] += h
+        tgt_m[pos] -= h
+        fd = (F_at(Gp, Up, Vp) - F_at(Gm, Um, Vm)) / (2 * h)
+        an = gG[pos] if kind == "G" else (gU[k][pos] if kind == "U" else gV[k][pos])
+        assert an == pytest.approx(fd, rel=1e-6, abs=1e-7), (kind, k, pos)
+    # w = -e reproduces the gradient of f
+    o.set_params(*params)
+    e = x - o.predict(idx)
+    for a, b in zip([*o.full_gradient(w=-e)], [*o.full_gradient()]):
+        for u, v in zip(a if isinstance(a, list) else [a], b if isinstance(b, list) else [b]):
+            np.testing.assert_allclose(u, v, rtol=1e-12, atol=1e-13)
+
+
 def test_untouched_rows_have_zero_gradient():
     prob, params = random_problem((10, 4, 4), (2, 2, 2), nnz=6, n_coupled=0, seed=9)
     o = make(prob, params, lambda_reg=0.5)
