@@ -28,9 +28,13 @@
  *     scalar to the host (s3_loss, s3_rmse) synchronise that stream; the others only
  *     enqueue work, except where stated.
  *   - Every call returns S3_OK or a negative status.  Invalid arguments and out-of-range
- *     indices are detected on the host before any kernel runs; no input can make a
- *     kernel fault.  After S3_ERR_CUDA the context is marked failed and every later call
- *     returns S3_ERR_STATE; s3_last_error() gives the text of the last error.
+ *     indices are detected before any parameter is read with them: on the host for every
+ *     array the library copies in (s3_init, s3_set_test, host-pointer s3_rmse), and by a
+ *     check inside the kernel for the index arrays that stay in the caller's device memory
+ *     (s3_predict, device-pointer s3_rmse, s3_rmse_noalloc): such an entry reads nothing and
+ *     the call returns S3_ERR_INDEX.  No input can make a kernel fault.  After S3_ERR_CUDA
+ *     the context is marked failed and every later call returns S3_ERR_STATE;
+ *     s3_last_error() gives the text of the last error.
  */
 #ifndef S3CMTF_H_
 #define S3CMTF_H_
@@ -94,8 +98,8 @@ typedef struct {
                            threads per entry; tiles of up to T / 4 spread each entry over
                            four), a 4-way tile T.  0 = default: T / 2 for 3-way tensors up to
                            rank 20 (192 at rank 10), 64 above, 128 with cp = 1, T for 4-way.
-                           The BF16 kernel's tiles (at most 128) are sized to hold as many
-                           entries in flight as the FP32 form. */
+                           The BF16 kernel takes tiles of 128 entries (fewer only when a
+                           tile's slots would not fit in shared memory). */
     float hog_staleness;/* HOGWILD: gamma of the staleness-aware row step.  A row expected to
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by
@@ -104,8 +108,8 @@ typedef struct {
                            entry's step grows stiffer with the rank); < 0 disables the
                            scaling. */
     int hog_ctas;       /* HOGWILD: CTAs working at once (0 = default: on 3-way tensors, enough
-                           for about 29184 tensor entries in flight in either form, at most as
-                           many as fit on the GPU; on 4-way tensors as many as fit).
+                           for at most about 29184 tensor entries in flight in either form, at
+                           most as many as fit on the GPU; on 4-way tensors as many as fit).
                            Fewer CTAs mean fewer stale updates in flight and less throughput. */
     int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = one per
                            SM, at most as many as fit); fewer CTAs make its grid-wide
@@ -124,6 +128,15 @@ typedef struct {
                            (HOGWILD).  Both precisions, and S3CMTF-CP.  The initial core may
                            hold negative entries until its first step; the factors start
                            non-negative (U(0,1)).  0 = the plain method. */
+    int grad_chunk;     /* s3_gradient: items of the visiting order per chunk of the gradient
+                           pass (its row-gradient slots are sized by one chunk's events);
+                           0 = default 1048576.  Deterministic for a given value; the
+                           compensated sums are carried across chunks. */
+    int hog_core_sync;  /* BF16 HOGWILD: tiles over which a CTA accumulates its tiles' core steps
+                           (in tensor memory) before adding them to G, lock-free, and re-reading
+                           the core; between two such points the CTA computes with its own BF16
+                           copy of the core.  0 = default: 1 at computed rank 16, 2 at 20, 4 at
+                           32.  1 = the per-tile core step of the FP32 form. */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.
@@ -177,22 +190,33 @@ int s3_epoch(s3_ctx* ctx, int mode, int precision);
 int s3_loss(s3_ctx* ctx, double* f_out, double* train_rmse_out);
 
 /* test RMSE of Section 4.1 over the given entries (no clipping).  test == NULL uses the
- * entries given to the last s3_set_test.  Host or device pointers per device_ptrs.
- * Synchronises. */
+ * entries given to the last s3_set_test.  Host or device pointers per device_ptrs; host
+ * indices are checked on the host, device indices by the kernel (S3_ERR_INDEX, no RMSE
+ * written, when one lies outside its mode's range).  Synchronises. */
 int s3_rmse(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs, double* rmse_out);
 
 /* Keep a copy of test entries on the device for s3_rmse(ctx, NULL, ...). */
 int s3_set_test(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs);
 
 /* Predictions x~ (Eq. (4)) at n coordinates: idx = host array of N device pointers each
- * [n]; out = device [n] FP32. */
+ * [n] (0-based int32); out = device [n] FP32, caller-owned.  An index outside [0, I_n)
+ * is caught inside the kernel: that entry reads no parameter and gets NaN, and the call
+ * returns S3_ERR_INDEX.  Synchronises (to read that check). */
 int s3_predict(s3_ctx* ctx, const int32_t* const* idx, int64_t n, float* out);
 
-/* Full gradient of f (sum over all train and coupled entries of Eq. (8)) at the current
- * parameters, written to caller-owned device buffers of the parameter shapes:
- * dG [prod J], dU[n] [I_n * J_n], dV[m] [K_m * J_c].  Rows without observed entries get
- * zero.  Deterministic (fixed-order segmented reductions with compensated FP32 sums). */
-int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* const* dV);
+/* Full gradient (Eq. (8) summed over all train and coupled entries, the adjoint of the
+ * tensor pass) at the current parameters, written to caller-owned device buffers of the
+ * parameter shapes: dG [prod J], dU[n] [I_n * J_n], dV[m] [K_m * J_c].
+ *   w   NULL: the gradient of f (Eq. (7)): every tensor entry's data terms carry -e_alpha.
+ *       Else device [nnz] FP32 weights in the train-entry order given to s3_init: entry
+ *       alpha's data terms carry w_alpha in place of -e_alpha, i.e.
+ *         dU^(n)_i = sum_{alpha: i_n = i} w_alpha p_n(alpha) + lambda_reg u^(n)_i,
+ *         dG       = sum_alpha w_alpha a_1 o .. o a_N + lambda_reg G,
+ *       with the coupled-matrix terms of Eq. (8) unchanged (w = -e gives the same result as
+ *       NULL).  The weights are read during the call; the library keeps no reference.
+ * Rows without observed entries get zero.  Deterministic (fixed-order segmented reductions
+ * with compensated FP32 sums). */
+int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const* dU, float* const* dV);
 
 /* Copy the parameters out to / in from caller-owned device buffers (shapes as above).
  * Used for checkpoint/resume (with s3_set_epoch) and to inject parameters. */
@@ -244,22 +268,35 @@ enum { S3_K_ALL = -1, S3_K_TENSOR_HOG = 0, S3_K_TENSOR_MB = 1, S3_K_TENSOR_GRAD 
 int s3_profile(s3_ctx* ctx, int enable);
 int s3_profile_read(s3_ctx* ctx, int family, double* ms, int64_t* launches, int64_t* entries);
 
+/* Measurement support: the FP32 CUDA-core roof of the current device, measured.  Every SM
+ * runs 64 warps of 16 independent FMA chains each, once with scalar FFMA and once with the
+ * packed two-lane FFMA2; each rate (TFLOP/s, 2 flop per lane-FMA) is the best of three
+ * launches of about 0.2 s timed with CUDA events on a private stream.  sm_mhz receives the
+ * device's nominal maximum SM clock.  No context needed; changes no device setting.  Any
+ * output may be NULL. */
+int s3_measure_fp32_peak(double* ffma_tflops, double* ffma2_tflops, double* sm_mhz);
+
 /* Test RMSE without allocating: the same value as s3_rmse(ctx, test, 1, ...) for callers
- * that cannot allocate device memory -- code running inside a CUDA graph capture, under a
- * fixed memory budget, or next to an allocator that owns the whole device -- while s3_rmse
- * may grow its reduction buffer with cudaMalloc.  The paper has no counterpart; it is a
- * deployment variant of the reduction of Section 4.1's test RMSE.
+ * that must not allocate device memory while they run -- a process whose memory pool or
+ * caching allocator has reserved the whole device (a cudaMalloc would fail or fragment it),
+ * a job held to a fixed device-memory budget that was accounted up front, or a serving loop
+ * that cannot take the device-wide synchronisation a cudaMalloc or cudaFree may cause --
+ * while s3_rmse may grow its reduction buffer with cudaMalloc.  The paper has no
+ * counterpart.
  *   idx       host array of N device pointers, each [n] (0-based int32 coordinates)
  *   val       device [n] observed values
- *   n         at most 2,097,152; larger n returns S3_ERR_ARG (split the call)
+ *   n         at most 2,097,152; larger n returns S3_ERR_ARG before any device work (split
+ *             the call)
  *   rmse_out  host; sqrt(sum (val - x~)^2 / n)
- * Its only scratch is a 64 KiB static device array compiled into the library (every GPU
- * that loads the library holds it until exit).  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) with the context's device current; make
- * that first call before any stream capture.  Calls share the array: calls whose work
- * overlaps on the GPU (other host threads, other streams) race on it and must be
- * serialised by the caller.  Enqueues on the context's stream and synchronises it.
- * Indices are not validated (they are device memory). */
+ * Its only scratch is one static device array of about 64 KiB compiled into the library
+ * (every GPU that loads the library holds it until the process exits).  The context's device
+ * must be current (S3_ERR_ARG otherwise).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+ * capture.  Calls share the array, which keeps the last call's contents: calls whose work
+ * overlaps on the GPU (other host threads, other streams, other contexts on the same
+ * device) race on it and must be serialised by the caller.  An index outside its mode's
+ * range is caught inside the kernel and returns S3_ERR_INDEX.  Enqueues on the context's
+ * stream and synchronises it. */
 int s3_rmse_noalloc(s3_ctx* ctx, const int32_t* const* idx, const float* val, int64_t n,
                     double* rmse_out);
 

@@ -21,7 +21,7 @@ LIB = os.path.join(BUILD, "libs3cmtf.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SOURCES = ["capi.cu", "k_tensor.cu", "k_tensor_hog2.cu", "k_tensor_hog4.cu", "k_tensor_bf16.cu",
-                "k_misc.cu", "k_minibatch.cu", "k_qr.cu", "k_cp.cu", "noalloc.cu"]
+                "k_misc.cu", "k_minibatch.cu", "k_qr.cu", "k_cp.cu", "noalloc.cu", "k_peak.cu"]
 CXX_SOURCES = ["layout.cpp"]
 
 

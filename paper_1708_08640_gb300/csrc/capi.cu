@@ -61,6 +61,7 @@ struct s3_ctx {
     size_t cp_smem = 0;             // S3CMTF-CP kernel's dynamic shared memory
     size_t hog_bf_smem = 0;
     int64_t hog_tile = 0, hog_per_sm = 0, hog_bf_per_sm = 0, hog_bf_tile = 0, hog_ccap = 0;
+    int hog_bf_sync = 1;            // BF16 HOGWILD: tiles between two core steps of a CTA
     double* qr_parts = nullptr;     // final QR step scratch (allocated at its first call)
     double* qr_R = nullptr;
     int* qr_bad = nullptr;
@@ -80,6 +81,9 @@ struct s3_ctx {
     int* h_flag = nullptr;         // pinned
     int* d_tile_counter = nullptr; // HOGWILD tile claims
     int* d_kerr = nullptr;         // set by a kernel whose bounded wait ran out
+    int* d_idx_bad = nullptr;      // set by the forward kernel on an out-of-range index
+    int* h_idx_bad = nullptr;      // pinned
+    float* grad_w = nullptr;       // s3_gradient's weights in the gradient grouping's order
     float* grad_comp = nullptr;    // compensation buffers of the gradient (all parameters)
     int64_t grad_comp_n = 0;
     float* values_stage = nullptr; // s3_update_values staging (nnz + sum ynnz floats)
@@ -315,7 +319,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
         hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0 || (hp->cp != 0 && hp->cp != 1) ||
-        (hp->nonneg != 0 && hp->nonneg != 1))
+        (hp->nonneg != 0 && hp->nonneg != 1) || hp->grad_chunk < 0 || hp->hog_core_sync < 0)
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];
@@ -451,39 +455,33 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
             ctx->hog_per_sm = cps;
         }
     }
-    // The BF16 form runs as many CTAs as fit (with hog_ctas as a cap), and its tiles hold as
-    // many entries as make the FP32 form's number in flight (at most 128, the MMA's M): both
-    // forms then take the same lock-free schedule, and differ by their arithmetic only.  Its
-    // grouping is built for two CTAs per SM first, and again for one when that grouping's
-    // shared memory does not let two fit.
+    // The BF16 form takes full tiles of 128 entries (the MMA's M) when its shared memory
+    // allows, and as many CTAs as fit (two per SM at rank 16, one above), capped by hog_ctas
+    // and, on 3-way tensors without hog_ctas, by the same budget of entries in flight as the
+    // FP32 form's default (kHogInflight).  Smaller tiles only when a tile's row slots and
+    // coupled entries would not fit.
     int64_t bf_tile = tensor_hog_bf16_tile();
     if (msg.empty() && bf16_ok) {
-        const int64_t inflight = ctx->hog_grid * tile;
-        auto ctas_for = [&](int want) {
-            int64_t c = (int64_t)want * ctx->num_sms;
-            return hp->hog_ctas > 0 ? std::min<int64_t>(c, hp->hog_ctas) : c;
-        };
-        auto tile_for = [&](int64_t ctas) {
-            return std::max<int64_t>(16, std::min<int64_t>(tensor_hog_bf16_tile(),
-                                                           inflight / std::max<int64_t>(ctas, 1)));
-        };
-        for (int want = 2; want >= 1; --want) {
-            const int64_t ctas = ctas_for(want);
-            bf_tile = tile_for(ctas);
+        ctx->hog_bf_sync = hp->hog_core_sync > 0 ? hp->hog_core_sync : tensor_hog_bf16_core_sync(ctx->bf_jp);
+        for (int64_t t = tensor_hog_bf16_tile(); t >= 16; t -= 32) {
+            bf_tile = t;
             hhog_bf = HostGrouping{};
             msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, bf_tile, POS_SLOT, hhog_bf);
             if (!msg.empty()) break;
             const size_t smem = tensor_hog_bf16_smem(ctx->bf_jp, hhog_bf.max_ev, hhog_bf.max_seg, nF);
             const int per_sm = smem <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->bf_jp, smem) : 0;
-            if (per_sm >= want || want == 1 || tile_for(ctas_for(want - 1)) == bf_tile) {
-                ctx->hog_bf_grid = per_sm >= want ? ctas : ctas_for(std::max(per_sm, 1));
+            if (per_sm >= 1 || t - 32 < 16) {
+                int64_t ctas = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
+                if (hp->hog_ctas > 0) ctas = std::min<int64_t>(ctas, hp->hog_ctas);
+                else ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, kHogInflight / bf_tile));
+                ctx->hog_bf_grid = per_sm >= 1 ? ctas : 0;
                 ctx->hog_bf_per_sm = std::max(per_sm, 1);
                 ctx->hog_bf_tile = bf_tile;
                 break;
             }
         }
     }
-    const int64_t grad_chunk = 1 << 20;
+    const int64_t grad_chunk = hp->grad_chunk > 0 ? hp->grad_chunk : 1 << 20;
     if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad, kShortSeg,
                                              kHugeSeg);
     if (!msg.empty()) return bail(S3_ERR_ARG, msg);
@@ -546,6 +544,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(dalloc(ctx, &ctx->d_flag, 1));
     CK(dalloc(ctx, &ctx->d_tile_counter, 1));
     CK(dalloc(ctx, &ctx->d_kerr, 1));
+    CK(dalloc(ctx, &ctx->d_idx_bad, 1));
+    CK(cudaMallocHost((void**)&ctx->h_idx_bad, sizeof(int)));
     CK(dalloc(ctx, &ctx->d_bar, 2));
     CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
     // one CTA per SM by default: the epoch's grid-wide barriers cost more with every CTA
@@ -627,6 +627,7 @@ extern "C" void s3_destroy(s3_ctx* ctx) {
     if (ctx->h_red) cudaFreeHost(ctx->h_red);
     if (ctx->h_eta) cudaFreeHost(ctx->h_eta);
     if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+    if (ctx->h_idx_bad) cudaFreeHost(ctx->h_idx_bad);
     delete ctx;
 }
 
@@ -734,8 +735,8 @@ static int enqueue_hogwild_bf16(s3_ctx* ctx) {
     CK(cudaMemsetAsync(ctx->d_tile_counter, 0, sizeof(int), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     KL(launch_tensor_hog_bf16(ctx->bf_jp, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
-                              ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid, D.max_ev,
-                              D.max_seg, ctx->d_kerr, ctx->stream));
+                              ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid,
+                              ctx->hog_bf_sync, D.max_ev, D.max_seg, ctx->d_kerr, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
     return S3_OK;
@@ -798,7 +799,8 @@ extern "C" int s3_loss(s3_ctx* ctx, double* f_out, double* rmse_out) {
     const int32_t* idx[kMaxN];
     for (int n = 0; n < N; ++n) idx[n] = ctx->grad.d.tidx[n];
     CK(prof_mark(ctx, S3_K_TENSOR_FWD));
-    KL(launch_tensor_fwd(N, ctx->JP, ctx->P, idx, ctx->grad.d.tval, ctx->nnz, nullptr, parts_a, ctx->stream));
+    KL(launch_tensor_fwd(N, ctx->JP, ctx->P, idx, ctx->I, nullptr, ctx->grad.d.tval, ctx->nnz, nullptr,
+                         parts_a, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_FWD));
     prof_count(ctx, S3_K_TENSOR_FWD, ctx->nnz);
     KL(launch_reduce_f64(parts_a, tb, ctx->d_red + 0, ctx->stream));
@@ -910,13 +912,21 @@ extern "C" int s3_rmse(s3_ctx* ctx, const s3_coo_tensor* test, int device_ptrs, 
     const int tb = tensor_fwd_blocks(n);
     int rc;
     if ((rc = ensure_red(ctx, tb)) != S3_OK) return rc;
+    // indices the library did not copy and check itself are checked by the kernel
+    const bool unchecked = test && device_ptrs;
+    if (unchecked) CK(cudaMemsetAsync(ctx->d_idx_bad, 0, sizeof(int), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_FWD));
-    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, val, n, nullptr, ctx->red_parts, ctx->stream));
+    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, ctx->I, unchecked ? ctx->d_idx_bad : nullptr,
+                         val, n, nullptr, ctx->red_parts, ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_FWD));
     prof_count(ctx, S3_K_TENSOR_FWD, n);
     KL(launch_reduce_f64(ctx->red_parts, tb, ctx->d_red, ctx->stream));
     CK(cudaMemcpyAsync(ctx->h_red, ctx->d_red, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    *ctx->h_idx_bad = 0;
+    if (unchecked)
+        CK(cudaMemcpyAsync(ctx->h_idx_bad, ctx->d_idx_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    if (*ctx->h_idx_bad) return fail(ctx, S3_ERR_INDEX, "s3_rmse: a test index lies outside its mode's range");
     *rmse_out = sqrt(ctx->h_red[0] / (double)n);
     return S3_OK;
 }
@@ -925,12 +935,19 @@ extern "C" int s3_predict(s3_ctx* ctx, const int32_t* const* idx, int64_t n, flo
     if (!usable(ctx)) return S3_ERR_STATE;
     if (n < 0 || (n > 0 && (!idx || !out))) return fail(ctx, S3_ERR_ARG, "invalid predict arguments");
     if (n == 0) return S3_OK;
-    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, nullptr, n, out, nullptr, ctx->stream));
+    for (int k = 0; k < ctx->N; ++k)
+        if (!idx[k]) return fail(ctx, S3_ERR_ARG, "s3_predict: an index pointer is NULL");
+    CK(cudaMemsetAsync(ctx->d_idx_bad, 0, sizeof(int), ctx->stream));
+    KL(launch_tensor_fwd(ctx->N, ctx->JP, ctx->P, idx, ctx->I, ctx->d_idx_bad, nullptr, n, out, nullptr,
+                         ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_idx_bad, ctx->d_idx_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (*ctx->h_idx_bad) return fail(ctx, S3_ERR_INDEX, "s3_predict: an index lies outside its mode's range");
     return S3_OK;
 }
 
 // ------------------------------------------------------------------ gradient
-extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* const* dV) {
+extern "C" int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const* dU, float* const* dV) {
     if (!usable(ctx)) return S3_ERR_STATE;
     const int N = ctx->N, M = ctx->M, nF = N + M;
     if (!dG || !dU || (M > 0 && !dV)) return fail(ctx, S3_ERR_ARG, "gradient outputs missing");
@@ -953,8 +970,14 @@ extern "C" int s3_gradient(s3_ctx* ctx, float* dG, float* const* dU, float* cons
         CK(cudaMemsetAsync(outs[F], 0, (size_t)(factor_rows(ctx, F) * factor_cols(ctx, F)) * sizeof(float), ctx->stream));
     }
     DevGrouping& D = ctx->grad;
+    if (w) {
+        // the caller's weights, from the order given to s3_init into the grouping's order
+        if (!ctx->grad_w) CK(dalloc(ctx, &ctx->grad_w, (size_t)ctx->nnz));
+        KL(launch_gather_f32(ctx->grad_w, w, D.t_src, ctx->nnz, ctx->stream));
+    }
     for (int64_t g = 0; g < D.ngroups; ++g) {
         TensorLaunch L{};
+        L.w = w ? ctx->grad_w : nullptr;
         L.e_begin = D.t_off[(size_t)g];
         L.e_end = D.t_off[(size_t)g + 1];
         for (int n = 0; n < N; ++n) L.contrib[n] = ctx->contrib[n];
@@ -1151,12 +1174,14 @@ extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* co
 
 // ------------------------------------------------------------------ accessors for noalloc.cu
 namespace s3 {
-const DParams* ctx_params(const s3_ctx* ctx, int* N, int* JP, cudaStream_t* stream, int* device) {
+const DParams* ctx_params(const s3_ctx* ctx, int* N, int* JP, cudaStream_t* stream, int* device,
+                          const int64_t** dims) {
     if (!usable(ctx)) return nullptr;
     *N = ctx->N;
     *JP = ctx->JP;
     *stream = ctx->stream;
     *device = ctx->device;
+    *dims = ctx->I;
     return &ctx->P;
 }
 int ctx_fail(s3_ctx* ctx, int code, const char* msg) { return fail(ctx, code, msg); }

@@ -106,10 +106,10 @@ __device__ __forceinline__ void hog_coupled(const DParams& P, const DGroup& Gr, 
 // A tile's segment table, per factor and segment: (row, first slot, events, step scale),
 // 16 bytes, in shared memory, with the segment counts, for a tile whose array ranges are in
 // shared memory (slo / shi, the lanes of hog_ranges).  hog_tables_async issues the first
-// three words as cp.async copies and stores the counts; once every thread has waited for its
-// copies (cp_async_wait_all) and a CTA barrier has passed, hog_tables_damp gathers each
-// segment's step scale (indexed by the segment's row) the same way; the flush reads the
-// table after a second wait and barrier.  No thread stalls on these loads: the table is
+// three words as cp.async copies and stores the counts; once a thread has waited for its own
+// copies (cp_async_wait_all), hog_tables_damp gathers the step scale of each segment it
+// copied (indexed by the segment's row) the same way; the flush reads the table after a
+// second wait and a barrier.  No thread stalls on these loads: the table is
 // needed only by the flush, so its round trips overlap the tile's arithmetic.  Threads
 // first, first + stride, ... take part.
 __device__ __forceinline__ void hog_tables_async(const DParams& P, const DGroup& Gr,
@@ -129,11 +129,11 @@ __device__ __forceinline__ void hog_tables_async(const DParams& P, const DGroup&
     }
 }
 
-__device__ __forceinline__ void hog_tables_damp(const DGroup& Gr, float* smem, const HogSmem& H,
+__device__ __forceinline__ void hog_tables_damp(const DParams& P, const DGroup& Gr, const int64_t* slo,
+                                                const int64_t* shi, float* smem, const HogSmem& H,
                                                 int first, int stride) {
-    const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
     for (int F = 0; F < H.nF; ++F) {
-        const int ns = cnts[F];
+        const int ns = (int)(shi[1 + P.M + F] - slo[1 + P.M + F]);
         int* tab = reinterpret_cast<int*>(smem + H.toff[F]);
         for (int l = first; l < ns; l += stride) cp_async4(tab + 4 * l + 3, Gr.row_damp[F] + tab[4 * l]);
     }
@@ -166,10 +166,11 @@ __device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, c
 // apply tile t's row steps: per touched row and 4 components, the sum of its slots in slot
 // order, then one vector atomic, step = -eta * (step scale of the row) * (sum or mean of the
 // row's gradients in the tile).  Slot rows hold JPR floats; global rows P.ld <= JPR, whose
-// P.ld / 4 quads are written.
+// P.ld / 4 quads are written.  Threads first, first + stride, ... take the (segment, quad)
+// items.
 template <int JPR>
 __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, const HogSmem& H,
-                                          float eta, int row_mean) {
+                                          float eta, int row_mean, int first, int stride) {
     constexpr int SS = slot_stride(JPR);
     const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
     const int nq = P.ld / 4;
@@ -178,7 +179,7 @@ __device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, c
         const float* sa = smem + H.off[F];
         const int4* tab = reinterpret_cast<const int4*>(smem + H.toff[F]);
         float* base = F < P.N ? P.U[F] : P.V[F - P.N];
-        for (int l = threadIdx.x; l < nseg * nq; l += blockDim.x) {
+        for (int l = first; l < nseg * nq; l += stride) {
             const int s = l / nq, q = l % nq;
             const int4 sg = tab[s];   // row, first slot, events, step scale
             const int32_t rr = sg.x, st = sg.y, cnt = sg.z;

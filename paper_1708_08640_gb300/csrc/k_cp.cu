@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
             for (int j = 0; j < JP; ++j) s_red[warp][j] = gd[j];
         cp_async_wait_all();   // this thread's table copies
         __syncthreads();
-        hog_tables_damp(Gr, smem, H, tid, kCpThreads);
+        hog_tables_damp(P, Gr, s_lo, s_hi, smem, H, tid, kCpThreads);
         // G_jj += eta cs / W (sum_b e_b prod_n a_n[j] / n_t - lambda_reg / |Omega| G_jj)
         if (tid < JP && nb > 0) {
             float s = 0.f;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
         // s_lo / s_hi / s_nxt past the barrier above until the one below)
         int64_t lo = 0, hi = 0;
         if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
-        hog_flush<JPR>(P, smem, H, eta, row_mean);
+        hog_flush<JPR>(P, smem, H, eta, row_mean, threadIdx.x, blockDim.x);
         __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
         if (tid < 32) {
             s_lo[tid] = lo;

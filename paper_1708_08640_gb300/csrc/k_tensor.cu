@@ -18,8 +18,13 @@
 
 namespace s3 {
 
+// Coordinates of the forward kernel: SoA index arrays, each mode's extent I_n, and an
+// optional flag raised when some index lies outside [0, I_n) (the entry is then skipped:
+// no row is read for it, its prediction is NaN and it adds nothing to the sums).
 struct IdxPtrs {
     const int32_t* p[kMaxN];
+    int32_t lim[kMaxN];
+    int* bad;
 };
 
 template <int N, int JP>
@@ -58,7 +63,9 @@ __global__ void __launch_bounds__(kTile) k_tensor_contrib(DParams P, DGroup Gr, 
                 load_row<JP, false>(P.U[n] + (int64_t)row[n] * JPR, a[n]);
             }
             float p[N][JP];
-            const float err = __ldg(Gr.tval + e) - entry_partials<N, JP>(sG, a, p);
+            const float xt = entry_partials<N, JP>(sG, a, p);
+            // the data terms' weight -err: the error (loss) or the caller's weight
+            const float err = L.w ? -__ldg(L.w + e) : __ldg(Gr.tval + e) - xt;
 #pragma unroll
             for (int n = 0; n < N; ++n) {
                 const float r = P.lambda_reg * __ldg(P.inv_cnt[n] + row[n]);
@@ -115,10 +122,21 @@ __global__ void __launch_bounds__(kTile) k_tensor_fwd(DParams P, IdxPtrs idx, co
     Kahan k;
     k.init();
     for (int64_t e = (int64_t)blockIdx.x * kTile + threadIdx.x; e < n; e += (int64_t)gridDim.x * kTile) {
+        int32_t r[N];
+        bool inside = true;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            r[m] = __ldg(idx.p[m] + e);
+            inside = inside && (uint32_t)r[m] < (uint32_t)idx.lim[m];
+        }
+        if (!inside) {
+            if (idx.bad) atomicExch(idx.bad, 1);
+            if (pred) pred[e] = __int_as_float(0x7fc00000);
+            continue;
+        }
         float a[N][JP];
 #pragma unroll
-        for (int m = 0; m < N; ++m)
-            load_row<JP, false>(P.U[m] + (int64_t)__ldg(idx.p[m] + e) * JPR, a[m]);
+        for (int m = 0; m < N; ++m) load_row<JP, false>(P.U[m] + (int64_t)r[m] * JPR, a[m]);
         const float xt = entry_predict<N, JP>(sG, a);
         if (pred) pred[e] = xt;
         if (x) {
@@ -196,12 +214,21 @@ cudaError_t launch_tensor_hog(int N, int JP, int L, const DParams& P, const DGro
                                  core_step_scale, max_events, max_segs, ccap, s);
 }
 
-cudaError_t launch_tensor_fwd(int N, int JP, const DParams& P, const int32_t* const* idx,
-                              const float* x, int64_t n, float* pred, float* sq_part,
-                              cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+static IdxPtrs idx_ptrs(int N, const int32_t* const* idx, const int64_t* dims, int* bad) {
     IdxPtrs ip;
-    for (int m = 0; m < kMaxN; ++m) ip.p[m] = m < N ? idx[m] : nullptr;
+    for (int m = 0; m < kMaxN; ++m) {
+        ip.p[m] = m < N ? idx[m] : nullptr;
+        ip.lim[m] = m < N ? (int32_t)dims[m] : 0;
+    }
+    ip.bad = bad;
+    return ip;
+}
+
+cudaError_t launch_tensor_fwd(int N, int JP, const DParams& P, const int32_t* const* idx,
+                              const int64_t* dims, int* bad, const float* x, int64_t n,
+                              float* pred, float* sq_part, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const IdxPtrs ip = idx_ptrs(N, idx, dims, bad);
     const unsigned grid = (unsigned)std::min<int64_t>((n + kTile - 1) / kTile, 4096);
     const size_t smem = sizeof(float) * core_floats(N, JP);
 #define X(NN, JJ)                                                                 \
@@ -234,10 +261,10 @@ int tensor_hog_blocks_per_sm(int N, int JP, int L, size_t smem) {
 
 // the forward pass with one CTA per 256 entries (no grid-stride loop): ceil(n / 256) pairs
 cudaError_t launch_tensor_fwd_one_pass(int N, int JP, const DParams& P, const int32_t* const* idx,
-                                       const float* x, int64_t n, float* sq_part, cudaStream_t s) {
+                                       const int64_t* dims, int* bad, const float* x, int64_t n,
+                                       float* sq_part, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    IdxPtrs ip;
-    for (int m = 0; m < kMaxN; ++m) ip.p[m] = m < N ? idx[m] : nullptr;
+    const IdxPtrs ip = idx_ptrs(N, idx, dims, bad);
     const unsigned grid = (unsigned)((n + kTile - 1) / kTile);
     const size_t smem = sizeof(float) * core_floats(N, JP);
 #define X(NN, JJ)                                                                      \

@@ -3,18 +3,30 @@
 // (16, 16), (20, 32) or (32, 32) (see BfLayout).  The parameters keep the context's FP32
 // layout (rows of P.ld floats, the core P.jp x P.jp x P.ldg); the kernel zero-extends them.
 //
-// A CTA of 128 threads takes tiles of 128 tensor entries (the MMA's M), one entry per
-// thread and TMEM lane.  The three dense contractions of the per-entry work run on the
-// 5th-generation tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32
-// accumulators in tensor memory), chunk by chunk of 128 (j1, j2) pairs:
-//   stage 1   T  = A3 . G_(3)^T      [128 entries x 128 pairs]   (Def. 4, Alg. 3: the core
-//                                      contracted with the last mode's rows)
-//   partial   P3 = KR . G_(3)        [128 entries x JK]           (p_3 = G x_{-3} {a})
-//   core      dG = KR^T . (e o A3)   [128 pairs x JK]             (sum_b e_b a1 o a2 o a3)
-// with KR[b] = a1_b (x) a2_b (the Khatri-Rao row of the entry).  The rest runs on CUDA cores
-// in FP32: p_1 = T a_2, p_2 = T^T a_1 and x~ = a_1 . p_1 from each thread's TMEM lane, the
-// error e = x - x~, the row gradients of Eq. (8) and the row / core steps.  FP32 master
-// parameters; BF16 only for the tensor-core operands.
+// A CTA takes tiles of up to 128 tensor entries (the MMA's M), one entry per thread of its
+// four entry warps and per TMEM lane.  The three dense contractions of the per-entry work
+// run on the 5th-generation tensor cores (tcgen05.mma, BF16 operands in shared memory, FP32
+// accumulators in tensor memory):
+//   stage 1   T  = A3 . G_(3)^T      [128 entries x 64 pairs] per MMA group, double-buffered
+//                                      (Def. 4, Alg. 3: the core contracted with the last
+//                                      mode's rows)
+//   partial   P3 = KR . G_(3)        [128 entries x JK]        (p_3 = G x_{-3} {a})
+//   core      dG += KR^T . (e o A3)  [128 pairs x JK] per chunk (sum_b e_b a1 o a2 o a3)
+// with KR[b] = a1_b (x) a2_b (the Khatri-Rao row of the entry), in chunks of 128 pairs.  The
+// rest runs on CUDA cores in FP32: p_1 = T a_2, p_2 = T^T a_1 and x~ = a_1 . p_1 from each
+// thread's TMEM lane (packed two-lane FMAs), the error e = x - x~, the row gradients of
+// Eq. (8) and the row steps.  FP32 master parameters; BF16 only for the tensor-core operands.
+//
+// A fifth warp issues every MMA (one elected thread) and hands buffers back and forth with
+// the entry warps through mbarriers, so that the MMAs of the next 64 pairs run while the
+// entry warps read the current ones, and the next Khatri-Rao chunk is built while the
+// current one is multiplied.
+//
+// The core step: a tile's core gradient (its entries' mean, e / n_b folded into e o A3)
+// accumulates in TMEM across the tiles a CTA takes, and is added to G (lock-free,
+// red.global.add) every `core_sync` tiles, when the CTA also re-reads the current core into
+// its BF16 copy; between two such points the CTA computes with its copy.  With core_sync = 1
+// this is the per-tile core step of the FP32 form.
 //
 // Shared-memory operands (no swizzle, 8 x 16-byte core matrices; see tc.cuh):
 //   sG   the core, element (j3, pair) at (pair/8)*(JK/8)*128 + (j3/8)*128 + (j3%8)*16
@@ -23,9 +35,8 @@
 //   sA3  K-major A of stage 1 (M = entry, K = j3)
 //   sKR  one 128-pair chunk, K-major A of the partial (M = entry, K = pair) and, read as
 //        MN-major, the A operand of the core GEMM (M = pair, K = entry)
-//   sEA3 e*a3, MN-major B of the core GEMM (K = entry, N = j3)
-// TMEM (256 columns, so that two CTAs share an SM): T of one chunk [0, 128), P3
-// [128, 128 + JK), dG of one chunk [128 + JK, 128 + 2 JK).
+//   sEA3 (e / n_b) a3, MN-major B of the core GEMM (K = entry, N = j3)
+// TMEM: dG of every chunk [0, NC JK), P3 [COL_P3, + JK), two stage-1 buffers of 64 columns.
 #include <cuda_runtime.h>
 
 #include "hog_common.cuh"
@@ -34,12 +45,14 @@
 
 namespace s3 {
 
-constexpr int kBfTile = 128;    // entries per tile (the MMA's M)
-constexpr int kChunk = 128;     // pairs per chunk (the N of stage 1, the M of the core GEMM)
+constexpr int kBfTile = 128;    // entries per tile at most (the MMA's M)
+constexpr int kChunk = 128;     // pairs per Khatri-Rao chunk (the M of the core GEMM)
+constexpr int kTN = 64;         // pairs per stage-1 MMA group (its N)
+constexpr int kNB = 2;          // stage-1 TMEM buffers
+constexpr int kBfThreads = kBfTile + 32;   // four entry warps and the MMA warp
 constexpr int kWaitLimit = 1 << 24;
-constexpr uint32_t kTmemCols = 256;
-// more than a third of an SM's shared memory, so that no more than two CTAs (2 x 256 TMEM
-// columns) are ever resident on one SM
+// shared memory of at least a third of an SM, so that no more than two CTAs share one (their
+// TMEM allocations of 256 columns then fit together)
 constexpr size_t kBfMinSmem = 80 * 1024;
 
 // JQ: the side of the (j1, j2) pair grid (the rank of modes 1 and 2 the kernel computes
@@ -50,9 +63,11 @@ template <int JQ, int JK>
 struct BfLayout {
     static_assert((JQ == 16 && JK == 16) || (JQ == 20 && JK == 32) || (JQ == 32 && JK == 32),
                   "the BF16 form is built for padded ranks 16, 20 and 32");
+    static_assert(JQ % 2 == 0, "pairs (2k, 2k + 1) share j1");
     static constexpr int NQ = JQ * JQ;                                  // pairs of the grid
     static constexpr int NPAIR = (NQ + kChunk - 1) / kChunk * kChunk;   // in whole chunks
     static constexpr int NC = NPAIR / kChunk;
+    static constexpr int NH = NPAIR / kTN;                              // stage-1 MMA groups
     static constexpr uint32_t G_BYTES = JK * NPAIR * 2;
     static constexpr uint32_t A3_BYTES = kBfTile * JK * 2;
     static constexpr uint32_t KR_BYTES = kBfTile * kChunk * 2;
@@ -62,11 +77,27 @@ struct BfLayout {
     static constexpr uint32_t OFF_KR = OFF_A3 + A3_BYTES;
     static constexpr uint32_t OFF_EA3 = OFF_KR + KR_BYTES;
     static constexpr uint32_t OFF_SLOTS = OFF_EA3 + EA3_BYTES;   // row gradient slots (floats)
-    static constexpr uint32_t COL_T = 0;
-    static constexpr uint32_t COL_P3 = kChunk;
-    static constexpr uint32_t COL_DG = kChunk + JK;
-    static_assert(COL_DG + JK <= kTmemCols, "TMEM budget");
+    // TMEM columns, each area 32-column aligned, the stage-1 buffers 64-column aligned
+    static constexpr uint32_t COL_DG = 0;
+    static constexpr uint32_t COL_P3 = (NC * JK + 31) / 32 * 32;
+    static constexpr uint32_t COL_T = (COL_P3 + JK + 63) / 64 * 64;
+    static constexpr uint32_t TMEM_USED = COL_T + kNB * kTN;
+    static constexpr uint32_t TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+    static_assert(TMEM_USED <= 512, "TMEM budget");
     static_assert(OFF_SLOTS % 16 == 0, "slot rows are written with 16-byte stores");
+    static constexpr int CTAS_PER_SM = TMEM_COLS == 256 ? 2 : 1;
+};
+
+// mbarriers of the kernel
+enum {
+    kBarA3 = 0,      // entry warps: the tile's A3 is in shared memory (or: no more tiles)
+    kBarKr = 1,      // entry warps: a Khatri-Rao chunk (and, first, e o A3) is in shared memory
+    kBarKrFree = 2,  // MMA warp: the MMAs reading the Khatri-Rao chunk have completed
+    kBarP3 = 3,      // MMA warp: the tile's P3 and dG MMAs have completed
+    kBarTFull = 4,   // [kNB] MMA warp: a stage-1 buffer holds its 64 pairs of T
+    kBarTFree = 4 + kNB,   // [kNB] entry warps: a stage-1 buffer has been read
+    kBarEnd = 4 + 2 * kNB,  // MMA warp: everything it issued has completed
+    kNBars = 5 + 2 * kNB
 };
 
 // one 16-byte chunk of 8 BF16 values
@@ -82,318 +113,452 @@ __device__ __forceinline__ uint32_t g_off(int pair, int j3) {
     return (uint32_t)((pair / 8) * (JK / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16 + (pair % 8) * 2);
 }
 
+// the entry warps' own barrier (the MMA warp runs a separate loop)
+__device__ __forceinline__ void entry_sync() {
+    asm volatile("bar.sync 1, %0;" :: "r"(kBfTile) : "memory");
+}
+
+__device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) {
+    return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// The current core as BF16 operand: coalesced float4 reads of G (the layout's
+// jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix layout
+// (pair = j1 JQ + j2); the padding past jp stays zero.  Eight loads in flight per thread.
 template <int JQ, int JK>
-__global__ void __launch_bounds__(kBfTile, 2)
+__device__ __forceinline__ void load_core_bf16(const DParams& P, uint8_t* smem_raw, int tid) {
+    using Lt = BfLayout<JQ, JK>;
+    constexpr int U = 8;
+    uint8_t* gb = smem_raw + Lt::OFF_G;
+    if (P.jp == JQ && P.ldg == JQ) {
+        // the layout's rank is the kernel's: compile-time divisions
+        constexpr int n4 = Lt::NQ * JQ / 4;                 // float4s
+        for (int b = 0; b < n4; b += kBfTile * U) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = b + u * kBfTile + tid;
+                v[u] = k < n4 ? ld4_cg(P.G + 4 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = b + u * kBfTile + tid;
+                if (k >= n4) continue;
+                const int l = 4 * k, pair = l / JQ, j0 = l % JQ;
+                const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(gb + g_off<JK>(pair, j0 + i)) = __float2bfloat16_rn(vv[i]);
+            }
+        }
+    } else {
+        const int jp = P.jp, ldg = P.ldg;
+        const int n4 = jp * jp * ldg / 4;
+        for (int b = 0; b < n4; b += kBfTile * U) {
+            float4 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = b + u * kBfTile + tid;
+                v[u] = k < n4 ? ld4_cg(P.G + 4 * k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int k = b + u * kBfTile + tid;
+                if (k >= n4) continue;
+                const int l = 4 * k, j3 = l % ldg, j12 = l / ldg;
+                const int pair = (j12 / jp) * JQ + j12 % jp;
+                const float vv[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    *reinterpret_cast<__nv_bfloat16*>(gb + g_off<JK>(pair, j3 + i)) = __float2bfloat16_rn(vv[i]);
+            }
+        }
+    }
+}
+
+template <int JQ, int JK>
+__global__ void __launch_bounds__(kBfThreads, BfLayout<JQ, JK>::CTAS_PER_SM)
 k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, const float* eta_p,
-                  int row_mean, float core_step_scale, HogSmem H, int* err_flag) {
+                  int row_mean, float core_step_scale, int core_sync, HogSmem H, int* err_flag) {
     using Lt = BfLayout<JQ, JK>;
     constexpr int JPR = JQ;          // slot rows (JQ is a multiple of 4)
     constexpr int NQ = Lt::NQ;
     constexpr int NC = Lt::NC;
+    constexpr int NH = Lt::NH;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     float* smem = reinterpret_cast<float*>(smem_raw);
     __shared__ uint32_t s_tmem;
-    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ __align__(8) uint64_t s_bar[kNBars];
     __shared__ int64_t s_cur, s_nxt;        // this tile and the one claimed after it
     __shared__ int64_t s_lo[32], s_hi[32];  // array ranges of this tile (hog_ranges lanes)
-    __shared__ int s_fail;   // set when a bounded wait ran out; read after barriers only
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int s_fail;   // set when a bounded wait ran out
+    __shared__ int s_go;     // the entry warps take another tile (read by the MMA warp)
+    __shared__ int s_fresh;  // the tile's core GEMM starts a new accumulation in TMEM
+    __shared__ int s_stop;   // thread 0's view of s_fail, the same for every entry thread
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const uint32_t sbase = smem_u32(smem_raw);
     const uint32_t sG = sbase + Lt::OFF_G;
     const uint32_t sA3 = sbase + Lt::OFF_A3;
     const uint32_t sKR = sbase + Lt::OFF_KR;
     const uint32_t sEA3 = sbase + Lt::OFF_EA3;
-    const __nv_bfloat16* gbf = reinterpret_cast<const __nv_bfloat16*>(smem_raw + Lt::OFF_G);
-    const float eta = *eta_p;
-    if (warp == 0) tmem_alloc(&s_tmem, kTmemCols);
+    if (warp == 0) tmem_alloc(&s_tmem, Lt::TMEM_COLS);
     if (tid == 0) {
-        mbar_init(&s_mbar, 1);
+        mbar_init(&s_bar[kBarA3], kBfTile / 32);
+        mbar_init(&s_bar[kBarKr], kBfTile / 32);
+        mbar_init(&s_bar[kBarKrFree], 1);
+        mbar_init(&s_bar[kBarP3], 1);
+        for (int b = 0; b < kNB; ++b) {
+            mbar_init(&s_bar[kBarTFull + b], 1);
+            mbar_init(&s_bar[kBarTFree + b], kBfTile / 32);
+        }
+        mbar_init(&s_bar[kBarEnd], 1);
         s_fail = 0;
+        s_fresh = 1;
     }
     // the BF16 core's padding (past the layout's jp, ldg) is zero for the whole launch
-    for (int l = tid * 16; l < (int)Lt::G_BYTES; l += kBfTile * 16)
-        st_shared_v4(sbase + Lt::OFF_G + l, 0u, 0u, 0u, 0u);
+    for (int l = tid * 16; l < (int)Lt::G_BYTES; l += kBfThreads * 16)
+        st_shared_v4(sG + l, 0u, 0u, 0u, 0u);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
-    uint32_t phase = 0;
 
-    // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
-    // starts with its ranges (entries, coupled entries, segments) in shared memory: its
-    // segment table goes out as asynchronous copies at once, and its critical path is the
-    // entries' index loads, then their rows.
-    if (tid == 0) {
-        s_cur = atomicAdd(tile_counter, 1);
-        s_nxt = atomicAdd(tile_counter, 1);
-    }
-    __syncthreads();
-    if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
-    __syncthreads();
-    for (;;) {
-        const int64_t t = s_cur;
-        if (t >= n_tiles || s_fail) break;
-        // the tile after the next one is claimed now; it is needed only at this one's end
-        int claim = 0;
-        if (tid == 0) claim = atomicAdd(tile_counter, 1);
-        hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
-        // ---- this thread's entry: indices first, so that their round trip overlaps the
-        //      core's reload
-        const int64_t e0 = s_lo[0];
-        const int nb = (int)(s_hi[0] - e0);
-        const bool valid = tid < nb;
-        const int64_t e = e0 + tid;
-        int32_t row[3] = {0, 0, 0};
-        int32_t tp[3] = {0, 0, 0};
-        float x = 0.f;
-        if (valid) {
-#pragma unroll
-            for (int n = 0; n < 3; ++n) {
-                row[n] = __ldg(Gr.tidx[n] + e);
-                tp[n] = __ldg(Gr.tpos[n] + e);
-            }
-            x = __ldg(Gr.tval + e);
-        }
-        // ---- the current core as BF16 operand: coalesced float4 reads of G (the layout's
-        //      jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix
-        //      layout (pair = j1 JQ + j2); the padding past jp stays zero
-        if (P.jp == JQ && P.ldg == JQ) {
-            // the layout's rank is the kernel's: pair = l / JQ with compile-time divisions
-            for (int l = tid * 4; l < NQ * JQ; l += kBfTile * 4) {
-                const float4 v = ld4_cg(P.G + l);
-                const int pair = l / JQ, j0 = l % JQ;
-                const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JK>(pair, j0 + i)) =
-                        __float2bfloat16_rn(vv[i]);
-            }
-        } else {
-            const int jp = P.jp, ldg = P.ldg;
-            for (int l = tid * 4; l < jp * jp * ldg; l += kBfTile * 4) {
-                const float4 v = ld4_cg(P.G + l);
-                const int j3 = l % ldg, j12 = l / ldg;
-                const int pair = (j12 / jp) * JQ + j12 % jp;
-                const float vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    *reinterpret_cast<__nv_bfloat16*>(smem_raw + Lt::OFF_G + g_off<JK>(pair, j3 + i)) =
-                        __float2bfloat16_rn(vv[i]);
-            }
-        }
-        // ---- the entry's rows, and the rows' 1 / |Omega^{n,i}| (used after the MMAs)
-        float a1[JQ], a2[JQ], a3[JK];
-        float inv[3] = {0.f, 0.f, 0.f};
-        if (valid) {
-            load_row_ld<JQ>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
-            load_row_ld<JQ>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
-            load_row_ld<JK>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
-#pragma unroll
-            for (int n = 0; n < 3; ++n) inv[n] = __ldg(P.inv_cnt[n] + row[n]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < JQ; ++j) { a1[j] = 0.f; a2[j] = 0.f; }
-#pragma unroll
-            for (int j = 0; j < JK; ++j) a3[j] = 0.f;
-        }
-        // A3 row (K-major, M = entry)
-#pragma unroll
-        for (int kg = 0; kg < JK / 8; ++kg) {
-            const uint32_t off = (tid / 8) * (JK / 8) * 128 + kg * 128 + (tid % 8) * 16;
-            st_shared_v4(sA3 + off, pack_bf16x2(a3[8 * kg], a3[8 * kg + 1]),
-                         pack_bf16x2(a3[8 * kg + 2], a3[8 * kg + 3]),
-                         pack_bf16x2(a3[8 * kg + 4], a3[8 * kg + 5]),
-                         pack_bf16x2(a3[8 * kg + 6], a3[8 * kg + 7]));
-        }
-        fence_proxy_async();
-        tc_fence_before();
-        __syncthreads();
-        // ---- stage 1, chunk by chunk; p1 and p2 from this thread's lane of T
-        float p1[JQ], p2[JQ];
-#pragma unroll
-        for (int j = 0; j < JQ; ++j) { p1[j] = 0.f; p2[j] = 0.f; }
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            if (tid == 0) {
+    if (warp == kBfTile / 32) {
+        // ------------------------------------------------------------ the MMA warp
+        if (lane == 0) {
+            uint32_t ph_a3 = 0, nh = 0, nk = 0;
+            bool ok = true;
+            for (;;) {
+                if (!mbar_wait(&s_bar[kBarA3], ph_a3, kWaitLimit)) { ok = false; break; }
+                ph_a3 ^= 1;
+                if (!s_go) break;
+                const bool fresh = s_fresh != 0;
                 tc_fence_after();
-                constexpr uint32_t idesc = tc_idesc_bf16(128, kChunk, 0, 1);
+                // stage 1: T[buffer] = A3 . G_(3)^T over 64 pairs (M = 128, N = 64, K = JK)
+                constexpr uint32_t id_t = tc_idesc_bf16(128, kTN, 0, 1);
+                for (int h = 0; h < NH && ok; ++h, ++nh) {
+                    const uint32_t b = nh % kNB;
+                    if (nh >= (uint32_t)kNB &&
+                        !mbar_wait(&s_bar[kBarTFree + b], ((nh / kNB) - 1) & 1, kWaitLimit)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
 #pragma unroll
-                for (int ks = 0; ks < JK / 16; ++ks) {
-                    const uint64_t ad = tc_sdesc(sA3 + ks * 256, 128, (JK / 8) * 128);
-                    const uint64_t bd = tc_sdesc(sG + (kChunk / 8) * c * (JK / 8) * 128 + ks * 256,
-                                                 128, (JK / 8) * 128);
-                    tc_mma(tmem + Lt::COL_T, ad, bd, idesc, ks > 0);
+                    for (int ks = 0; ks < JK / 16; ++ks) {
+                        const uint64_t ad = tc_sdesc(sA3 + ks * 256, 128, (JK / 8) * 128);
+                        const uint64_t bd = tc_sdesc(sG + (kTN / 8) * h * (JK / 8) * 128 + ks * 256, 128,
+                                                     (JK / 8) * 128);
+                        tc_mma(tmem + Lt::COL_T + b * kTN, ad, bd, id_t, ks > 0);
+                    }
+                    tc_commit(&s_bar[kBarTFull + b]);
                 }
-                tc_commit(&s_mbar);
+                if (!ok) break;
+                // the Khatri-Rao chunks: P3 += KR . G_(3)[chunk], dG[chunk] += KR^T . (e o A3)
+                constexpr uint32_t id_p3 = tc_idesc_bf16(128, JK, 0, 0);
+                constexpr uint32_t id_dg = tc_idesc_bf16(128, JK, 1, 1);
+                for (int c = 0; c < NC; ++c, ++nk) {
+                    if (!mbar_wait(&s_bar[kBarKr], nk & 1, kWaitLimit)) { ok = false; break; }
+                    tc_fence_after();
+#pragma unroll
+                    for (int ks = 0; ks < kChunk / 16; ++ks) {
+                        const uint64_t ad = tc_sdesc(sKR + ks * 256, 128, (kChunk / 8) * 128);
+                        const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JK / 8) * 128,
+                                                     (JK / 8) * 128, 128);
+                        tc_mma(tmem + Lt::COL_P3, ad, bd, id_p3, (c > 0 || ks > 0));
+                    }
+#pragma unroll
+                    for (int ks = 0; ks < kBfTile / 16; ++ks) {
+                        const uint64_t ad = tc_sdesc(sKR + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
+                        const uint64_t bd = tc_sdesc(sEA3 + ks * 256, 128, (kBfTile / 8) * 128);
+                        tc_mma(tmem + Lt::COL_DG + c * JK, ad, bd, id_dg, (!fresh || ks > 0));
+                    }
+                    tc_commit(&s_bar[kBarKrFree]);
+                    if (c == NC - 1) tc_commit(&s_bar[kBarP3]);
+                }
+                if (!ok) break;
             }
-            if (!mbar_wait(&s_mbar, phase, kWaitLimit)) s_fail = 1;
-            phase ^= 1;
-            tc_fence_after();
-#pragma unroll
-            for (int q = 0; q < kChunk / 32; ++q) {
-                float v[32];
-                tmem_ld32(lane_base + Lt::COL_T + 32 * q, v);
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int pair = kChunk * c + 32 * q + i;
-                    if (pair >= NQ) continue;   // past the grid (its T is zero)
-                    const int j1 = pair / JQ, j2 = pair % JQ;
-                    p1[j1] = fmaf(v[i], a2[j2], p1[j1]);
-                    p2[j2] = fmaf(v[i], a1[j1], p2[j2]);
-                }
+            if (!ok) s_fail = 1;
+            // nothing this thread issued may still run when the TMEM is released
+            tc_commit(&s_bar[kBarEnd]);
+            if (!mbar_wait(&s_bar[kBarEnd], 0, kWaitLimit)) s_fail = 1;
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ the entry warps
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
+        const float eta = *eta_p;
+        uint32_t ph_p3 = 0, nh = 0, nk = 0;
+        int since_sync = 0, acc_tiles = 0;
+        // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
+        // starts with its ranges (entries, coupled entries, segments) in shared memory.
+        if (tid == 0) {
+            s_cur = atomicAdd(tile_counter, 1);
+            s_nxt = atomicAdd(tile_counter, 1);
+        }
+        entry_sync();
+        if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
+        load_core_bf16<JQ, JK>(P, smem_raw, tid);
+        fence_proxy_async();
+        if (tid == 0) s_go = s_cur < n_tiles;
+        entry_sync();
+        for (;;) {
+            if (!s_go) {
+                // the MMA warp learns that no tile follows
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_bar[kBarA3]);
+                break;
             }
-            // every lane has read T before the next chunk's MMA overwrites it; after the
-            // last chunk, every thread's table copies have landed too
-            if (c == NC - 1) cp_async_wait_all();
-            tc_fence_before();
-            __syncthreads();
-        }
-        // the segments' step scales, gathered by the rows the table copies brought
-        hog_tables_damp(Gr, smem, H, tid, kBfTile);
-        float xt = 0.f;
+            // the tile after the next one is claimed now; it is needed only at this one's end
+            int claim = 0;
+            if (tid == 0) claim = atomicAdd(tile_counter, 1);
+            hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
+            // ---- this thread's entry and its rows
+            const int64_t e0 = s_lo[0];
+            const int nb = (int)(s_hi[0] - e0);
+            const bool valid = tid < nb;
+            const int64_t e = e0 + tid;
+            int32_t row[3] = {0, 0, 0};
+            int32_t tp[3] = {0, 0, 0};
+            float x = 0.f;
+            if (valid) {
 #pragma unroll
-        for (int j = 0; j < JQ; ++j) xt = fmaf(a1[j], p1[j], xt);
-        const float err = valid ? x - xt : 0.f;
-        // e * a3 (MN-major B of the core GEMM: K = entry, N = j3)
-#pragma unroll
-        for (int jg = 0; jg < JK / 8; ++jg) {
-            const uint32_t off = jg * (kBfTile / 8) * 128 + (tid / 8) * 128 + (tid % 8) * 16;
-            st_shared_v4(sEA3 + off, pack_bf16x2(err * a3[8 * jg], err * a3[8 * jg + 1]),
-                         pack_bf16x2(err * a3[8 * jg + 2], err * a3[8 * jg + 3]),
-                         pack_bf16x2(err * a3[8 * jg + 4], err * a3[8 * jg + 5]),
-                         pack_bf16x2(err * a3[8 * jg + 6], err * a3[8 * jg + 7]));
-        }
-        // ---- partial p3 and core gradient, chunk by chunk of Khatri-Rao rows; each chunk's
-        //      share of the core step leaves as soon as its dG is in TMEM:
-        //      G += eta cs / W (dG / n_t - lambda_reg / |Omega| G)   (lock-free)
-        const float sc = nb > 0 ? eta * core_step_scale / (float)nb : 0.f;
-        const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-#pragma unroll
-            for (int kg = 0; kg < kChunk / 8; ++kg) {
-                float w[8];
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int pair = kChunk * c + 8 * kg + i;
-                    const int pq = pair < NQ ? pair : 0;   // (a compile-time index)
-                    w[i] = pair < NQ ? a1[pq / JQ] * a2[pq % JQ] : 0.f;
+                for (int n = 0; n < 3; ++n) {
+                    row[n] = __ldg(Gr.tidx[n] + e);
+                    tp[n] = __ldg(Gr.tpos[n] + e);
                 }
-                const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
-                st_shared_v4(sKR + off, pack_bf16x2(w[0], w[1]), pack_bf16x2(w[2], w[3]),
-                             pack_bf16x2(w[4], w[5]), pack_bf16x2(w[6], w[7]));
+                x = __ldg(Gr.tval + e);
+            }
+            float a1[JQ], a2[JQ], a3[JK];
+            float inv[3] = {0.f, 0.f, 0.f};
+            if (valid) {
+                load_row_ld<JQ>(P.U[0] + (int64_t)row[0] * P.ld, P.ld, a1);
+                load_row_ld<JQ>(P.U[1] + (int64_t)row[1] * P.ld, P.ld, a2);
+                load_row_ld<JK>(P.U[2] + (int64_t)row[2] * P.ld, P.ld, a3);
+#pragma unroll
+                for (int n = 0; n < 3; ++n) inv[n] = __ldg(P.inv_cnt[n] + row[n]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < JQ; ++j) { a1[j] = 0.f; a2[j] = 0.f; }
+#pragma unroll
+                for (int j = 0; j < JK; ++j) a3[j] = 0.f;
+            }
+            // A3 row (K-major, M = entry)
+#pragma unroll
+            for (int kg = 0; kg < JK / 8; ++kg) {
+                const uint32_t off = (tid / 8) * (JK / 8) * 128 + kg * 128 + (tid % 8) * 16;
+                st_shared_v4(sA3 + off, pack_bf16x2(a3[8 * kg], a3[8 * kg + 1]),
+                             pack_bf16x2(a3[8 * kg + 2], a3[8 * kg + 3]),
+                             pack_bf16x2(a3[8 * kg + 4], a3[8 * kg + 5]),
+                             pack_bf16x2(a3[8 * kg + 6], a3[8 * kg + 7]));
             }
             fence_proxy_async();
-            tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_bar[kBarA3]);
+            // ---- stage 1: p1 = T a2 and p2 = T^T a1 from this lane of T, 64 pairs at a time
+            float p1[JQ];
+            float2 p2v[JQ / 2];
+#pragma unroll
+            for (int j = 0; j < JQ; ++j) p1[j] = 0.f;
+#pragma unroll
+            for (int j = 0; j < JQ / 2; ++j) p2v[j] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int h = 0; h < NH; ++h, ++nh) {
+                const uint32_t b = nh % kNB;
+                if (!mbar_wait(&s_bar[kBarTFull + b], (nh / kNB) & 1, kWaitLimit)) s_fail = 1;
                 tc_fence_after();
-                // P3 += KR . G_(3)[chunk]   (M = 128 entries, N = JK, K = 128 pairs)
-                constexpr uint32_t id_p3 = tc_idesc_bf16(128, JK, 0, 0);
+                uint32_t r[2][32];
+                tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN, r[0]);
+                tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN + 32, r[1]);
+                tmem_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_bar[kBarTFree + b]);
+                // pairs h*64 + i, i even: (i, i + 1) share j1 (JQ is even); two running
+                // accumulators of p1[j1] keep the FMA chains short
+                float2 run[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                int run_j1 = -1;
 #pragma unroll
-                for (int ks = 0; ks < kChunk / 16; ++ks) {
-                    const uint64_t ad = tc_sdesc(sKR + ks * 256, 128, (kChunk / 8) * 128);
-                    const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JK / 8) * 128,
-                                                 (JK / 8) * 128, 128);
-                    tc_mma(tmem + Lt::COL_P3, ad, bd, id_p3, (c > 0 || ks > 0));
-                }
-                // dG[chunk] = KR^T . (e o A3)   (M = 128 pairs, N = JK, K = 128 entries)
-                constexpr uint32_t id_dg = tc_idesc_bf16(128, JK, 1, 1);
-#pragma unroll
-                for (int ks = 0; ks < kBfTile / 16; ++ks) {
-                    const uint64_t ad = tc_sdesc(sKR + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
-                    const uint64_t bd = tc_sdesc(sEA3 + ks * 256, 128, (kBfTile / 8) * 128);
-                    tc_mma(tmem + Lt::COL_DG, ad, bd, id_dg, ks > 0);
-                }
-                tc_commit(&s_mbar);
-            }
-            if (!mbar_wait(&s_mbar, phase, kWaitLimit)) s_fail = 1;
-            phase ^= 1;
-            tc_fence_after();
-            if (nb > 0) {
-                // lane tid holds pair kChunk*c + tid = j1 JQ + j2 (inside the layout when
-                // j1, j2 < jp, and then its j3 < ldg go out); the regulariser reads the BF16
-                // copy of G (its term, eta cs lambda / (W |Omega|) G, sits far below G's
-                // FP32 ulp)
-                const int pair = kChunk * c + tid;
-                const int j1 = pair / JQ, j2 = pair % JQ;
-                const bool inside = pair < NQ && j1 < P.jp && j2 < P.jp;
-                float* g = P.G + ((int64_t)j1 * P.jp + j2) * P.ldg;
-#pragma unroll
-                for (int h = 0; h < JK / 16; ++h) {
-                    float d[16];
-                    tmem_ld16(lane_base + Lt::COL_DG + 16 * h, d);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (!inside || 16 * h + 4 * q >= P.ldg) continue;
-                        float gv[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-                            gv[i] = __bfloat162float(gbf[g_off<JK>(pair, 16 * h + 4 * q + i) / 2]);
-                        red_add_v4(g + 16 * h + 4 * q, fmaf(sc, d[4 * q], -rg * gv[0]),
-                                   fmaf(sc, d[4 * q + 1], -rg * gv[1]),
-                                   fmaf(sc, d[4 * q + 2], -rg * gv[2]),
-                                   fmaf(sc, d[4 * q + 3], -rg * gv[3]));
-                        if (P.nonneg) red_proj_v4(g + 16 * h + 4 * q);
+                for (int i = 0; i < kTN; i += 2) {
+                    const int pair = h * kTN + i;
+                    if (pair >= NQ) break;   // past the grid (its T is zero)
+                    const int j1 = pair / JQ, j2 = pair % JQ;
+                    if (j1 != run_j1) {
+                        if (run_j1 >= 0)
+                            p1[run_j1] += (run[0].x + run[0].y) + (run[1].x + run[1].y);
+                        run[0] = make_float2(0.f, 0.f);
+                        run[1] = make_float2(0.f, 0.f);
+                        run_j1 = j1;
                     }
+                    const float2 tv = make_float2(__uint_as_float(r[i / 32][i % 32]),
+                                                  __uint_as_float(r[i / 32][i % 32 + 1]));
+                    run[(i / 2) & 1] = __ffma2_rn(tv, make_float2(a2[j2], a2[j2 + 1]), run[(i / 2) & 1]);
+                    p2v[j2 / 2] = __ffma2_rn(tv, make_float2(a1[j1], a1[j1]), p2v[j2 / 2]);
                 }
+                if (run_j1 >= 0) p1[run_j1] += (run[0].x + run[0].y) + (run[1].x + run[1].y);
             }
-            // every lane has read dG, and the MMAs have read KR, before the next chunk
-            tc_fence_before();
-            __syncthreads();
-        }
-        // ---- row gradients (Eq. (8)) into the tile's slots
-        {
-            float p3[JK];
+            // the segment table copies have landed; each segment's step scale is gathered
+            // by its row
+            cp_async_wait_all();
+            hog_tables_damp(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
+            float xt = 0.f;
 #pragma unroll
-            for (int h = 0; h < JK / 16; ++h) {
-                float v[16];
-                tmem_ld16(lane_base + Lt::COL_P3 + 16 * h, v);
-#pragma unroll
-                for (int i = 0; i < 16; ++i) p3[16 * h + i] = v[i];
-            }
+            for (int j = 0; j < JQ; ++j) xt = fmaf(a1[j], p1[j], xt);
+            const float err = valid ? x - xt : 0.f;
+            // ---- row gradients of modes 1 and 2 (Eq. (8)) into the tile's slots
             if (valid) {
                 const float r0 = P.lambda_reg * inv[0];
                 const float r1 = P.lambda_reg * inv[1];
-                const float r2 = P.lambda_reg * inv[2];
                 float c[JPR];
 #pragma unroll
                 for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p1[j], r0 * a1[j]);
                 put_slot<JPR>(smem, H, 0, tp[0], c);
 #pragma unroll
-                for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p2[j], r1 * a2[j]);
+                for (int j = 0; j < JQ / 2; ++j) {
+                    c[2 * j] = fmaf(-err, p2v[j].x, r1 * a2[2 * j]);
+                    c[2 * j + 1] = fmaf(-err, p2v[j].y, r1 * a2[2 * j + 1]);
+                }
                 put_slot<JPR>(smem, H, 1, tp[1], c);
-#pragma unroll
-                for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
-                put_slot<JPR>(smem, H, 2, tp[2], c);
             }
+            // ---- (e / n_b) a3: MN-major B of the core GEMM (K = entry, N = j3); the tile's
+            //      mean is folded in, so that dG accumulates means across tiles
+            {
+                const float w = nb > 0 ? err / (float)nb : 0.f;
+#pragma unroll
+                for (int jg = 0; jg < JK / 8; ++jg) {
+                    const uint32_t off = jg * (kBfTile / 8) * 128 + (tid / 8) * 128 + (tid % 8) * 16;
+                    st_shared_v4(sEA3 + off, pack_bf16x2(w * a3[8 * jg], w * a3[8 * jg + 1]),
+                                 pack_bf16x2(w * a3[8 * jg + 2], w * a3[8 * jg + 3]),
+                                 pack_bf16x2(w * a3[8 * jg + 4], w * a3[8 * jg + 5]),
+                                 pack_bf16x2(w * a3[8 * jg + 6], w * a3[8 * jg + 7]));
+                }
+            }
+            // ---- Khatri-Rao chunks: products of the BF16 rows, two per instruction
+            __nv_bfloat162 b1[JQ], b2[JQ / 2];
+#pragma unroll
+            for (int j = 0; j < JQ; ++j) b1[j] = __float2bfloat162_rn(a1[j]);
+#pragma unroll
+            for (int j = 0; j < JQ / 2; ++j) b2[j] = __floats2bfloat162_rn(a2[2 * j], a2[2 * j + 1]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c, ++nk) {
+                uint32_t kr[kChunk / 2];
+#pragma unroll
+                for (int i = 0; i < kChunk; i += 2) {
+                    const int pair = kChunk * c + i;
+                    const int pq = pair < NQ ? pair : 0;   // (a compile-time index)
+                    kr[i / 2] = pair < NQ ? bf2_bits(__hmul2(b1[pq / JQ], b2[(pq % JQ) / 2])) : 0u;
+                }
+                // the previous chunk's MMAs have read sKR
+                if (nk > 0 && !mbar_wait(&s_bar[kBarKrFree], (nk - 1) & 1, kWaitLimit)) s_fail = 1;
+#pragma unroll
+                for (int kg = 0; kg < kChunk / 8; ++kg) {
+                    const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
+                    st_shared_v4(sKR + off, kr[4 * kg], kr[4 * kg + 1], kr[4 * kg + 2], kr[4 * kg + 3]);
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_bar[kBarKr]);
+            }
+            // ---- P3, the mode-3 row gradient, the coupled entries
+            if (!mbar_wait(&s_bar[kBarP3], ph_p3, kWaitLimit)) s_fail = 1;
+            ph_p3 ^= 1;
+            tc_fence_after();
+            {
+                float p3[JK];
+#pragma unroll
+                for (int hh = 0; hh < JK / 16; ++hh) {
+                    float v[16];
+                    tmem_ld16(lane_base + Lt::COL_P3 + 16 * hh, v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) p3[16 * hh + i] = v[i];
+                }
+                if (valid) {
+                    const float r2 = P.lambda_reg * inv[2];
+                    float c[JPR];
+#pragma unroll
+                    for (int j = 0; j < JQ; ++j) c[j] = fmaf(-err, p3[j], r2 * a3[j]);
+                    put_slot<JPR>(smem, H, 2, tp[2], c);
+                }
+            }
+            hog_coupled<JQ>(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
+            cp_async_wait_all();
+            tc_fence_before();
+            if (tid == 0) s_stop = s_fail;
+            entry_sync();
+            // ---- the row steps; the next tile's ranges are read meanwhile (nothing reads
+            //      s_lo / s_hi / s_nxt past the barrier above until the one below).  A wait
+            //      that ran out leaves this tile's TMEM values undefined: nothing is written.
+            const bool failed = s_stop != 0;
+            int64_t lo = 0, hi = 0;
+            if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
+            if (!failed) hog_flush<JPR>(P, smem, H, eta, row_mean, tid, kBfTile);
+            since_sync += 1;
+            acc_tiles += nb > 0;
+            // ---- the core step of the tiles since the last one, when due (and always at the
+            //      CTA's last tile):  G += eta cs / W (sum of tile means - n lambda / |Omega| G)
+            const bool last = s_nxt >= n_tiles;
+            if (since_sync >= core_sync || last || failed) {
+                const float sc = eta * core_step_scale;
+                const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz * (float)acc_tiles;
+                const __nv_bfloat16* gbf = reinterpret_cast<const __nv_bfloat16*>(smem_raw + Lt::OFF_G);
+#pragma unroll 1
+                for (int c = 0; c < NC; ++c) {
+                    float d[JK];
+#pragma unroll
+                    for (int hh = 0; hh < JK / 16; ++hh) {
+                        float v[16];
+                        tmem_ld16(lane_base + Lt::COL_DG + c * JK + 16 * hh, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) d[16 * hh + i] = v[i];
+                    }
+                    // lane tid holds pair kChunk*c + tid = j1 JQ + j2 (inside the layout when
+                    // j1, j2 < jp, and then its j3 < ldg go out); the regulariser reads the
+                    // BF16 copy of G (its term sits far below G's FP32 ulp)
+                    const int pair = kChunk * c + tid;
+                    const int j1 = pair / JQ, j2 = pair % JQ;
+                    const bool inside = !failed && acc_tiles > 0 && pair < NQ && j1 < P.jp && j2 < P.jp;
+                    float* g = P.G + ((int64_t)j1 * P.jp + j2) * P.ldg;
+#pragma unroll
+                    for (int q = 0; q < JK / 4; ++q) {
+                        if (!inside || 4 * q >= P.ldg) continue;
+                        float gv[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) gv[i] = __bfloat162float(gbf[g_off<JK>(pair, 4 * q + i) / 2]);
+                        red_add_v4(g + 4 * q, fmaf(sc, d[4 * q], -rg * gv[0]),
+                                   fmaf(sc, d[4 * q + 1], -rg * gv[1]),
+                                   fmaf(sc, d[4 * q + 2], -rg * gv[2]),
+                                   fmaf(sc, d[4 * q + 3], -rg * gv[3]));
+                        if (P.nonneg) red_proj_v4(g + 4 * q);
+                    }
+                }
+                tc_fence_before();
+                entry_sync();    // every lane has read dG and the old copy before it changes
+                load_core_bf16<JQ, JK>(P, smem_raw, tid);
+                fence_proxy_async();
+                since_sync = 0;
+                acc_tiles = 0;
+                if (tid == 0) s_fresh = 1;
+            } else if (tid == 0) {
+                s_fresh = 0;
+            }
+            __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
+            if (tid < 32) {
+                s_lo[tid] = lo;
+                s_hi[tid] = hi;
+            }
+            if (tid == 0) {
+                s_cur = s_nxt;
+                s_nxt = claim;
+                s_go = s_cur < n_tiles && !failed;
+            }
+            entry_sync();
         }
-        hog_coupled<JQ>(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
-        cp_async_wait_all();
-        tc_fence_before();
-        __syncthreads();
-        // the next tile's ranges are read while this one's row steps go out (nothing reads
-        // s_lo / s_hi / s_nxt past the barrier above until the one below)
-        int64_t lo = 0, hi = 0;
-        if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
-        hog_flush<JPR>(P, smem, H, eta, row_mean);
-        __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
-        if (tid < 32) {
-            s_lo[tid] = lo;
-            s_hi[tid] = hi;
-        }
-        if (tid == 0) {
-            s_cur = s_nxt;
-            s_nxt = claim;
-        }
-        __syncthreads();
     }
     tc_fence_before();
     __syncthreads();
     if (s_fail && tid == 0) atomicExch(err_flag, 1);
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, kTmemCols);
+    if (warp == 0) tmem_dealloc(tmem, Lt::TMEM_COLS);
 }
 
 // JP: the rank the form computes at, 16, 20 or 32 (the slot rows hold JP floats)
@@ -413,8 +578,15 @@ size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* ma
 
 int tensor_hog_bf16_tile() { return kBfTile; }
 
-// the dynamic shared-memory limit, and the largest shared-memory carveout: two CTAs of this
-// kernel need most of an SM's shared memory
+int tensor_hog_bf16_core_sync(int JP) {
+    // tiles between two core steps of a CTA by default: about one per 8192 elements of the
+    // core the kernel computes with (1 at rank 16, 2 at 20, 4 at 32)
+    const int elems = JP == 16 ? 16 * 16 * 16 : JP == 20 ? 20 * 20 * 32 : 32 * 32 * 32;
+    const int k = (elems + 4095) / 8192;
+    return k < 1 ? 1 : k;
+}
+
+// the dynamic shared-memory limit, and the largest shared-memory carveout
 template <typename K>
 static cudaError_t prep_bf16(K kernel, size_t smem) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -427,20 +599,21 @@ static cudaError_t prep_bf16(K kernel, size_t smem) {
 template <int JQ, int JK>
 static cudaError_t launch_bf16(const DParams& P, const DGroup& G, int64_t n_tiles, int* tile_counter,
                                int grid, const float* eta, int row_mean, float core_step_scale,
-                               const HogSmem& H, size_t smem, int* err_flag, cudaStream_t s) {
+                               int core_sync, const HogSmem& H, size_t smem, int* err_flag,
+                               cudaStream_t s) {
     cudaError_t e = prep_bf16(k_tensor_hog_bf16<JQ, JK>, smem);
     if (e != cudaSuccess) return e;
-    k_tensor_hog_bf16<JQ, JK><<<grid, kBfTile, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
-                                                          core_step_scale, H, err_flag);
+    k_tensor_hog_bf16<JQ, JK><<<grid, kBfThreads, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
+                                                             core_step_scale, core_sync, H, err_flag);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
-                                   float core_step_scale, const int64_t* max_events,
+                                   float core_step_scale, int core_sync, const int64_t* max_events,
                                    const int64_t* max_segs, int* err_flag, cudaStream_t s) {
     const size_t fixed = bf16_fixed_bytes(JP);
-    if (!fixed || P.N != 3) return cudaErrorInvalidValue;
+    if (!fixed || P.N != 3 || core_sync < 1) return cudaErrorInvalidValue;
     if (n_tiles <= 0) return cudaSuccess;
     HogSmem H{};
     size_t smem = hog_smem_floats(JP, max_events, max_segs, P.N + P.M, &H, fixed / sizeof(float)) *
@@ -448,30 +621,35 @@ cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, in
     if (smem < kBfMinSmem) smem = kBfMinSmem;
     if (JP == 16)
         return launch_bf16<16, 16>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
-                                   H, smem, err_flag, s);
+                                   core_sync, H, smem, err_flag, s);
     if (JP == 20)
         return launch_bf16<20, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
-                                   H, smem, err_flag, s);
-    return launch_bf16<32, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale, H,
-                               smem, err_flag, s);
+                                   core_sync, H, smem, err_flag, s);
+    return launch_bf16<32, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
+                               core_sync, H, smem, err_flag, s);
 }
 
 // CTAs of the BF16 kernel that fit on one SM with this much dynamic shared memory (at most
-// two: two CTAs take all 512 TMEM columns), from the device's shared-memory and register
-// limits and the kernel's static resources.  (A CTA launched beyond what fits only runs once
-// another has finished: the kernel has no inter-CTA waits, so it would find no tile left.)
+// two at rank 16, one at ranks 20 and 32: their TMEM allocations of 256 or 512 columns must
+// fit together), from the device's shared-memory and register limits and the kernel's
+// static resources.  (A CTA launched beyond what fits only runs once another has finished:
+// the kernel has no inter-CTA waits, so it would find no tile left.)
 int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem) {
     cudaFuncAttributes fa{};
     cudaError_t e = cudaErrorInvalidValue;
+    int cap = 1;
     if (JP == 16) {
         e = prep_bf16(k_tensor_hog_bf16<16, 16>, smem);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<16, 16>);
+        cap = BfLayout<16, 16>::CTAS_PER_SM;
     } else if (JP == 20) {
         e = prep_bf16(k_tensor_hog_bf16<20, 32>, smem);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<20, 32>);
+        cap = BfLayout<20, 32>::CTAS_PER_SM;
     } else if (JP == 32) {
         e = prep_bf16(k_tensor_hog_bf16<32, 32>, smem);
         if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_tensor_hog_bf16<32, 32>);
+        cap = BfLayout<32, 32>::CTAS_PER_SM;
     }
     if (e != cudaSuccess) return 0;
     int dev = 0, sm_smem = 0, reserved = 0, sm_regs = 0;
@@ -484,9 +662,9 @@ int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem) {
     const int by_smem = (int)((size_t)sm_smem / per_cta);
     // registers are allocated per warp in units of 256
     const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
-    const int by_regs = sm_regs / (warp_regs * (kBfTile / 32));
+    const int by_regs = sm_regs / (warp_regs * (kBfThreads / 32));
     int nb = by_smem < by_regs ? by_smem : by_regs;
-    return nb < 2 ? nb : 2;
+    return nb < cap ? nb : cap;
 }
 
 }  // namespace s3

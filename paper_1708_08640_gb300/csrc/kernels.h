@@ -12,6 +12,8 @@ struct TensorLaunch {
     int64_t e_begin, e_end;      // tensor entries [e_begin, e_end) of the grouping
     float* contrib[kMaxN];       // per-mode contribution slots (minibatch / gradient)
     float* core_part;            // one partial core gradient per CTA, dense [prod JP]
+    const float* w;              // gradient pass: per-entry weights in grouping order that
+                                 // take the place of -(x - x~) in the data terms; null = -e
 };
 
 // Shared-memory bytes of the FP32 tensor kernels (for cudaFuncSetAttribute / launch).
@@ -39,17 +41,19 @@ cudaError_t launch_tensor_hog(int N, int JP, int L, const DParams& P, const DGro
                               int row_mean, float core_step_scale, const int64_t* max_events,
                               const int64_t* max_segs, int64_t ccap, cudaStream_t s);
 
-// BF16 tensor-core HOGWILD epoch (N = 3, JP = 16 or 32): as launch_tensor_hog with tiles of
-// tensor_hog_bf16_tile() entries, at most two CTAs per SM (tensor_hog_bf16_blocks_per_sm);
-// sets *err_flag when a bounded wait on the tensor cores ran out.
+// BF16 tensor-core HOGWILD epoch (N = 3, JP = 16, 20 or 32): as launch_tensor_hog with tiles
+// of at most tensor_hog_bf16_tile() entries, at most two CTAs per SM at rank 16 and one above
+// (tensor_hog_bf16_blocks_per_sm); each CTA adds its accumulated core steps to G every
+// core_sync tiles (and re-reads the core then); sets *err_flag when a bounded wait on the
+// tensor cores ran out.
 int tensor_hog_bf16_tile();
+int tensor_hog_bf16_core_sync(int JP);   // the default core_sync of a rank
 int tensor_hog_bf16_blocks_per_sm(int JP, size_t smem);
 size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF);
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
-                                   float core_step_scale, const int64_t* max_events,
-                                   const int64_t* max_segs, int* err_flag,
-                                   cudaStream_t s);
+                                   float core_step_scale, int core_sync, const int64_t* max_events,
+                                   const int64_t* max_segs, int* err_flag, cudaStream_t s);
 
 // Deterministic minibatch epoch as one cooperative launch of `grid` CTAs (see k_minibatch.cu).
 struct MbLaunch {
@@ -69,10 +73,16 @@ cudaError_t launch_minibatch_epoch(int N, int JP, const DParams& P, const DGroup
                                    const MbLaunch& L, cudaStream_t s);
 
 // Forward: x~ of n entries given as SoA index arrays; optional predictions out, optional
-// per-CTA compensated partial sums of (x - x~)^2 (2 floats per CTA).
+// per-CTA compensated partial sums of (x - x~)^2 (2 floats per CTA).  dims: host [N] mode
+// extents; an entry with an index outside [0, dims[m]) reads nothing, gets a NaN
+// prediction, adds nothing to the sums and sets *bad = 1 (bad may be null).
 cudaError_t launch_tensor_fwd(int N, int JP, const DParams& P, const int32_t* const* idx,
-                              const float* x, int64_t n, float* pred, float* sq_part,
-                              cudaStream_t s);
+                              const int64_t* dims, int* bad, const float* x, int64_t n,
+                              float* pred, float* sq_part, cudaStream_t s);
+// the same with one CTA per 256 entries (no grid-stride loop): ceil(n / 256) pairs
+cudaError_t launch_tensor_fwd_one_pass(int N, int JP, const DParams& P, const int32_t* const* idx,
+                                       const int64_t* dims, int* bad, const float* x, int64_t n,
+                                       float* sq_part, cudaStream_t s);
 
 int tensor_supported_jp(int N, int J);   // smallest instantiated JP >= J, or 0
 // Compute threads of a CTA of the FP32 HOGWILD kernel (it adds one prefetch warp): 384

@@ -40,7 +40,8 @@ class S3CMTF:
 
     def __init__(self, dims, J, train_idx, train_val, coupled=(), *, lr0=0.01, mu=0.1,
                  lambda_reg=0.01, lambda_m=1.0, batch=4096, core_scale=1.0, row_rule="sum",
-                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, cp=0, nonneg=0, seed=0,
+                 hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, cp=0, nonneg=0,
+                 grad_chunk=0, hog_core_sync=0, seed=0,
                  order=None,
                  device=None,
                  stream=None):
@@ -55,6 +56,7 @@ class S3CMTF:
         self.M = len(self.coupled)
         idx = _host(train_idx, np.int32)
         val = _host(train_val, np.float32)
+        self.nnz = int(val.shape[0])
         self._dims_arr = (C.c_int64 * self.N)(*self.dims)
         self._idx_rows = [np.ascontiguousarray(idx[n]) for n in range(self.N)]
         idx_ptrs = L.ptr_array([a.ctypes.data for a in self._idx_rows])
@@ -74,7 +76,7 @@ class S3CMTF:
         hp = L.s3_hparams(lr0, mu, lambda_reg, lambda_m, int(batch), core_scale,
                           _ROW[row_rule] if isinstance(row_rule, str) else int(row_rule),
                           int(hog_tile), float(hog_staleness), int(hog_ctas), int(mb_ctas),
-                          int(cp), int(nonneg))
+                          int(cp), int(nonneg), int(grad_chunk), int(hog_core_sync))
         Jarr = (C.c_int * self.N)(*self.J)
         order_arr = None if order is None else _host(order, np.int64)
         with torch.cuda.device(self.device):
@@ -184,13 +186,21 @@ class S3CMTF:
              for mode, K in self.coupled]
         return G, U, V
 
-    def gradient(self):
+    def gradient(self, w=None):
+        """The full gradient (s3_gradient).  w: None for the gradient of f, or per-entry
+        weights [nnz] (train-entry order) that take the place of -e in the data terms."""
         dG, dU, dV = self._param_buffers()
+        wd = None
+        if w is not None:
+            wd = _dev(w, torch.float32, self.device).reshape(-1)
+            if wd.numel() != self.nnz:
+                raise ValueError(f"w has {wd.numel()} entries, the model {self.nnz}")
         self._enter()
-        self._check(self.lib.s3_gradient(self.ctx, dG.data_ptr(),
+        self._check(self.lib.s3_gradient(self.ctx, None if wd is None else wd.data_ptr(),
+                                         dG.data_ptr(),
                                          L.ptr_array([u.data_ptr() for u in dU]),
                                          L.ptr_array([v.data_ptr() for v in dV])))
-        self._leave(dG, *dU, *dV)
+        self._leave(dG, *dU, *dV, *([] if wd is None else [wd]))
         return dG, dU, dV
 
     def get_params(self):

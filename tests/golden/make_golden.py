@@ -5,12 +5,17 @@ records a fingerprint of the generated inputs (so a test can verify it regenerat
 same data) and the test RMSE after every epoch of
   - the sequential epoch of Algorithm 1 (P = 1), and
   - the deterministic minibatch epoch (batch 4096, row sum, core_scale 32),
-starting from the seeded initial parameters and the seeded visiting order.  With the
-fourth argument ``nonneg`` it writes the curves of the non-negative form (projected SGD,
-Section 5) to curve_<workload>_<mode>_nonneg.json.
+starting from the seeded initial parameters and the seeded visiting order.  With
+``--nonneg`` it writes the curves of the non-negative form (projected SGD, Section 5) to
+curve_<workload>_<mode>_nonneg.json.  With ``--rank J`` the workload is fitted at ranks
+(J, J, J) (the rating workloads at other ranks, with the core step scale of that rank) and
+the file is curve_<workload>_j<J>_<mode>.json.  The file is rewritten after every epoch,
+so a long run leaves the epochs it has finished.
 
-usage: python tests/golden/make_golden.py cfg1_small [epochs] [modes] [nonneg]
+usage: python tests/golden/make_golden.py cfg1_small [--epochs 10]
+           [--modes sequential,minibatch] [--nonneg] [--rank J]
 """
+import argparse
 import hashlib
 import json
 import os
@@ -39,35 +44,42 @@ def fingerprint(p):
     return h.hexdigest()[:16]
 
 
-def curve(p, mode, epochs, hparams):
+def curve(p, mode, epochs, hparams, rec, path):
     o = oracle.Oracle(p, **hparams, **(MB if mode == "minibatch" else {}))
     o.set_params(*synth.init_params(p, 1))
     order = synth.union_order(p, 2)
-    out = []
+    t0 = time.time()
+    rec["test_rmse"] = []
     for t in range(epochs):
         (o.epoch_minibatch if mode == "minibatch" else o.epoch_sequential)(t, order)
-        out.append(o.rmse(p.test_idx, p.test_val))
-    return out
+        rec["test_rmse"].append(o.rmse(p.test_idx, p.test_val))
+        rec["epochs"] = t + 1
+        rec["seconds"] = round(time.time() - t0, 1)
+        json.dump(rec, open(path, "w"), indent=1)
+        print(mode, t, rec["test_rmse"][-1], rec["seconds"], flush=True)
 
 
 def main():
-    name = sys.argv[1]
-    epochs = int(sys.argv[2]) if len(sys.argv) > 2 else 10
-    modes = sys.argv[3].split(",") if len(sys.argv) > 3 else ["sequential", "minibatch"]
-    nonneg = len(sys.argv) > 4 and sys.argv[4] == "nonneg"
-    hparams = dict(HPARAMS, nonneg=1) if nonneg else HPARAMS
-    p = synth.make_problem(name)
-    for mode in modes:
-        t0 = time.time()
-        rec = dict(workload=name, mode=mode, recipe=p.recipe, fingerprint=fingerprint(p),
-                   hparams=hparams, minibatch=MB if mode == "minibatch" else None,
-                   init_seed=1, order_seed=2, epochs=epochs,
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--epochs", type=int, default=10)
+    ap.add_argument("--modes", default="sequential,minibatch")
+    ap.add_argument("--nonneg", action="store_true")
+    ap.add_argument("--rank", type=int, default=0)
+    a = ap.parse_args()
+    hparams = dict(HPARAMS, nonneg=1) if a.nonneg else dict(HPARAMS)
+    p = synth.make_problem(a.workload)
+    tag = a.workload
+    if a.rank:
+        p = synth.with_rank(p, (a.rank,) * p.N)
+        tag = f"{a.workload}_j{a.rank}"
+    for mode in a.modes.split(","):
+        rec = dict(workload=a.workload, rank=list(p.J), mode=mode, recipe=p.recipe,
+                   fingerprint=fingerprint(p), hparams=hparams,
+                   minibatch=MB if mode == "minibatch" else None, init_seed=1, order_seed=2,
                    source="oracle/ (FP64 CPU), written by tests/golden/make_golden.py")
-        rec["test_rmse"] = curve(p, mode, epochs, hparams)
-        rec["seconds"] = round(time.time() - t0, 1)
-        path = os.path.join(HERE, f"curve_{name}_{mode}{'_nonneg' if nonneg else ''}.json")
-        json.dump(rec, open(path, "w"), indent=1)
-        print(mode, rec["test_rmse"], flush=True)
+        path = os.path.join(HERE, f"curve_{tag}_{mode}{'_nonneg' if a.nonneg else ''}.json")
+        curve(p, mode, a.epochs, hparams, rec, path)
 
 
 if __name__ == "__main__":

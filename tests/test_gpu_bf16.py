@@ -17,16 +17,18 @@ from tests.oracle_cases import random_problem
 pytestmark = pytest.mark.gpu
 
 
-def one_tile_problem(J, seed=4, nnz=120):
+def one_tile_problem(J, seed=4, nnz=120, dims=(30, 20, 10)):
     # 120 entries: one tile of the FP32 kernel (128 entries, two lanes each) and of the
-    # BF16 kernel (128 entries); 60 entries: one tile of 64 (four lanes each)
-    prob, params = random_problem((30, 20, 10), (J, J, J), nnz=nnz, n_coupled=1, seed=seed,
+    # BF16 kernel (128 entries); 60 entries: one tile of 64 (four lanes each); 4-way
+    # tensors: one lane per entry, tiles of up to 256
+    N = len(dims)
+    prob, params = random_problem(dims, (J,) * N, nnz=nnz, n_coupled=1, seed=seed,
                                   coupled_nnz=nnz // 3, K=9)
     prob.train_val = f32(prob.train_val + 2.0)
     for c in prob.coupled:
         c.vals = f32(c.vals)
     G, U, V = params
-    G = G * np.sqrt(27.0 / J ** 3)
+    G = G * np.sqrt(3.0 ** N / J ** N)
     return prob, fp32_params((G, U, V))
 
 
@@ -49,16 +51,22 @@ def run_one_tile(prob, params, precision, lr0=0.01, tile=128):
     return (G, U, V), orc
 
 
-@pytest.mark.parametrize("J,tile,nnz", [(5, 128, 120), (16, 128, 120), (10, 64, 60)])
-def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J, tile, nnz):
+@pytest.mark.parametrize("J,tile,nnz,dims", [
+    (5, 128, 120, (30, 20, 10)), (16, 128, 120, (30, 20, 10)), (10, 64, 60, (30, 20, 10)),
+    (20, 128, 120, (30, 20, 10)), (32, 64, 60, (30, 20, 10)),
+    (8, 256, 200, (12, 10, 8, 6)), (7, 256, 256, (12, 10, 8, 6))])
+def test_fp32_hogwild_single_tile_is_group_step(cuda_lib, J, tile, nnz, dims):
     """1e-4 for the core: the HOGWILD kernel sums a tile's core gradients in plain FP32 (the
-    minibatch kernels compensate theirs); 1e-5 for the rows.  Tiles of 128 entries run two
-    lanes per entry, tiles of 64 four."""
-    prob, params = one_tile_problem(J, nnz=nnz)
+    minibatch kernels compensate theirs); 1e-5 for the rows.  3-way tiles of 128 entries
+    run two lanes per entry, tiles of 64 four (ranks 5, 10, 16, 20 and 32: every 3-way
+    instantiation the default launches use; rank 32 takes tiles of at most 64, its core
+    fills most of shared memory); 4-way tiles (rank 8, and rank 7 padded to 8, a full tile
+    of 256) one lane per entry."""
+    prob, params = one_tile_problem(J, nnz=nnz, dims=dims)
     (G, U, V), orc = run_one_tile(prob, params, "fp32", tile=tile)
     G0, U0, V0 = params
     assert_step_close(G.cpu().double().numpy(), orc.G, G0, 1e-4, "G")
-    for n in range(3):
+    for n in range(len(dims)):
         assert_step_close(U[n].cpu().double().numpy(), orc.U[n], U0[n], 1e-5, f"U{n}")
     assert_step_close(V[0].cpu().double().numpy(), orc.V[0], V0[0], 1e-5, "V")
 
