@@ -458,44 +458,58 @@ def nonneg_hogwild(p, order, stream, epochs=4):
 # ----------------------------------------------------------------------------- our arm
 SCAL_NNZ = (100_000, 1_000_000, 10_000_000, 100_000_000)     # at I = 10^4
 SCAL_I = (1_000, 10_000, 100_000, 1_000_000, 10_000_000, 100_000_000)   # at |Omega| = 10^6
+# the reduced sweep the default run carries (a few seconds of input generation)
+SCAL_NNZ_QUICK = (250_000, 1_000_000, 4_000_000, 16_000_000)
+SCAL_I_QUICK = (1_000, 10_000, 100_000)
 
 
-def run_scalability(args):
+def scalability_sweep(nnz_list, i_list, steps=3, warmup=1, stream=None):
     """Section 4.3 (data scalability): HOGWILD epoch time of the FP32 form on the synthetic
     I x I x I tensors, over |Omega| at I = 10^4 and over I at |Omega| = 10^6 (coupled
     I x I matrix with |Omega|/10 entries, J = 10).  The paper's claim: time linear in
-    |Omega|, independent of I.  Parameters from the library's seeded initialisation."""
+    |Omega|, independent of I.  Returns the per-point times, the least-squares line of time
+    over items with its R^2, and the largest / smallest time across I."""
     import torch
 
     from paper_1708_08640_gb300.model import S3CMTF
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
+    stream = stream or torch.cuda.Stream()
 
     def one(I, nnz):
         p = synth.make_problem(f"scal:{I}:{nnz}")
         m = S3CMTF.from_problem(p, order=synth.union_order(p, 2), stream=stream)
-        for _ in range(max(1, args.warmup)):
+        for _ in range(max(1, warmup)):
             m.epoch("hogwild")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             m.epoch("hogwild")
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         m.close()
         return {"I": I, "nnz": nnz, "train_nnz": p.nnz, "items": p.n_union, "ms_per_epoch": ms,
                 "nnz_updates_per_s": p.n_union / (ms / 1000.0)}
 
-    by_nnz = [one(10_000, n) for n in SCAL_NNZ]
-    by_i = [one(i, 1_000_000) for i in SCAL_I]
+    by_nnz = [one(10_000, n) for n in nnz_list]
+    by_i = [one(i, 1_000_000) for i in i_list]
     x = np.array([r["items"] for r in by_nnz], dtype=np.float64)
     y = np.array([r["ms_per_epoch"] for r in by_nnz])
     slope, icpt = np.polyfit(x, y, 1)
     r2 = 1.0 - np.sum((y - (slope * x + icpt)) ** 2) / np.sum((y - y.mean()) ** 2)
     ti = np.array([r["ms_per_epoch"] for r in by_i])
-    top = by_nnz[-1]
+    return {"over_nnz_at_I_1e4": by_nnz, "over_I_at_nnz_1e6": by_i,
+            "linear_fit_ms_per_item": float(slope), "linear_fit_intercept_ms": float(icpt),
+            "linear_fit_r2": float(r2), "time_ratio_max_over_min_across_I": float(ti.max() / ti.min())}
+
+
+def run_scalability(args):
+    """The full Section 4.3 sweeps (|Omega| from 10^5 to 10^8, I from 10^3 to 10^8) as the
+    bench line's step."""
+    import torch
+    torch.cuda.set_device(0)
+    sc = scalability_sweep(SCAL_NNZ, SCAL_I, args.steps, args.warmup)
+    top = sc["over_nnz_at_I_1e4"][-1]
     line = {"metric": METRIC, "value": top["nnz_updates_per_s"], "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": top["ms_per_epoch"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -503,10 +517,7 @@ def run_scalability(args):
             "config": {"workload": "Section 4.3 scalability: I x I x I uniform tensors, coupled "
                                    "I x I matrix with |Omega|/10 entries, J = 10, FP32 HOGWILD",
                        "parallelism": "replicas x1"},
-            "scalability": {"over_nnz_at_I_1e4": by_nnz, "over_I_at_nnz_1e6": by_i,
-                            "linear_fit_ms_per_item": slope, "linear_fit_intercept_ms": icpt,
-                            "linear_fit_r2": r2,
-                            "time_ratio_max_over_min_across_I": float(ti.max() / ti.min())}}
+            "scalability": sc}
     print(json.dumps(line), flush=True)
 
 

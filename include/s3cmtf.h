@@ -137,6 +137,14 @@ typedef struct {
                            the core; between two such points the CTA computes with its own BF16
                            copy of the core.  0 = default: 1 at computed rank 16, 2 at 20, 4 at
                            32.  1 = the per-tile core step of the FP32 form. */
+    int wait_limit_us;  /* how long a bounded wait inside an epoch kernel (the minibatch epoch's
+                           grid barrier, the BF16 kernel's tensor-core hand-offs) may last before
+                           the kernel gives up, records where, and the epoch returns S3_ERR_CUDA
+                           (the context is then failed; the device stays usable).  0 = default
+                           2000000 (2 s). */
+    int64_t device_bytes_cap;  /* the most device memory the context may allocate (its layout,
+                           parameters and scratch); an allocation beyond it fails with
+                           S3_ERR_OOM as if the device were full.  0 = no cap. */
 } s3_hparams;
 
 /* Create a context on the current CUDA device.
@@ -217,6 +225,31 @@ int s3_predict(s3_ctx* ctx, const int32_t* const* idx, int64_t n, float* out);
  * Rows without observed entries get zero.  Deterministic (fixed-order segmented reductions
  * with compensated FP32 sums). */
 int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const* dU, float* const* dV);
+
+/* Partitioned problems (one process per GPU; mode-1 rows split across the processes, each
+ * with the tensor entries and coupled entries of its rows, every other parameter replicated).
+ * s3_set_counts gives a context that holds one part the counts of the whole problem, which
+ * the regularisation terms of Eq. (7) and Eq. (8) use:
+ *   counts     host array of N + n_coupled pointers to host int64 arrays: for every tensor
+ *              factor row |Omega^{n,i}| (the whole problem's tensor entries in that row), then
+ *              for every coupled factor row |Omega_Y^{2,k}| (its coupled matrix's entries in
+ *              that column)
+ *   nnz_total  |Omega| of the whole problem
+ * It replaces the counts the context took from its own entries (S3_ERR_ARG, changing
+ * nothing, when a count is below the context's own or nnz_total below its nnz).  After it,
+ * s3_gradient returns this part's share of the whole problem's gradient: summed over the
+ * parts (an all-reduce) it is the whole gradient (Eq. (8) summed over every entry).  The
+ * HOGWILD step scales are not changed; s3_loss then counts this part's errors with the
+ * whole problem's regularisers.
+ * s3_apply_gradient takes one step of the minibatch rule whose group is a whole epoch, from
+ * the whole gradient (device buffers of the parameter shapes): rows u <- u - eta_t dU, coupled
+ * rows likewise, the core G <- G - eta_t core_scale dG / |Omega| (|Omega| = nnz_total), then
+ * the projection of the non-negative form; the epoch counter advances.  The same gradient
+ * applied by every part leaves identical replicas, and the step equals s3_epoch(S3_MINIBATCH)
+ * with one batch holding the whole problem.  Row rule S3_ROW_SUM only (else S3_ERR_ARG);
+ * S3_ERR_DIVERGED if a parameter became non-finite.  Synchronises. */
+int s3_set_counts(s3_ctx* ctx, const int64_t* const* counts, int64_t nnz_total);
+int s3_apply_gradient(s3_ctx* ctx, const float* dG, const float* const* dU, const float* const* dV);
 
 /* Copy the parameters out to / in from caller-owned device buffers (shapes as above).
  * Used for checkpoint/resume (with s3_set_epoch) and to inject parameters. */

@@ -47,6 +47,7 @@ class _Data(C.Structure):
         ("M", C.c_int), ("cmode", C.POINTER(C.c_int)), ("K", C.POINTER(C.c_int64)),
         ("ynnz", C.POINTER(C.c_int64)), ("yr", C.POINTER(C.POINTER(C.c_int32))),
         ("yc", C.POINTER(C.POINTER(C.c_int32))), ("y", C.POINTER(C.POINTER(C.c_double))),
+        ("cnt_total", C.POINTER(C.POINTER(C.c_int64))), ("nnz_total", C.c_int64),
     ]
 
 
@@ -110,7 +111,10 @@ def _ptr_array(arrs, ct):
 class Oracle:
     """FP64 model state plus the problem it is fitted to."""
 
-    def __init__(self, prob, hparams=None, **hp_overrides):
+    def __init__(self, prob, hparams=None, counts=None, nnz_total=0, **hp_overrides):
+        """counts, nnz_total: when prob is a part of a larger problem, that problem's row
+        counts (one int64 array per factor: U^(1..N), then V_m) and |Omega|, which the
+        regularisation terms use; None / 0 = prob's own."""
         self.lib = _lib_handle()
         self.dims = tuple(int(d) for d in prob.dims)
         self.J = tuple(int(j) for j in prob.J)
@@ -137,7 +141,13 @@ class Oracle:
             int(self._x.shape[0]), _ptr(self._idx, C.c_int32), _ptr(self._x, C.c_double),
             self.M, _ptr(self._cmode, C.c_int), _ptr(self._K, C.c_int64),
             _ptr(self._ynnz, C.c_int64), _ptr_array(self._yr, C.c_int32),
-            _ptr_array(self._yc, C.c_int32), _ptr_array(self._y, C.c_double))
+            _ptr_array(self._yc, C.c_int32), _ptr_array(self._y, C.c_double),
+            None, int(nnz_total))
+        if counts is not None:
+            self._cnt = [np.ascontiguousarray(c, dtype=np.int64) for c in counts]
+            assert len(self._cnt) == self.N + self.M
+            self._cnt_ptrs = _ptr_array(self._cnt, C.c_int64)
+            self.data.cnt_total = self._cnt_ptrs
         hp = dict(getattr(prob, "hparams", {}) or {})
         hp.update(hparams or {})
         hp.update(hp_overrides)

@@ -60,6 +60,11 @@ typedef struct {
     const int32_t* const* yr;    /* [M][ynnz] row index j1 into I_c */
     const int32_t* const* yc;    /* [M][ynnz] column index j2 into K */
     const double* const* y;      /* [M][ynnz] */
+    /* a part of a larger problem: that problem's row counts (N + M arrays: |Omega^{n,i}| for
+       every tensor factor row, then |Omega_Y^{2,k}| for every coupled factor row) and its
+       |Omega|, used by the regularisation terms; NULL / 0 = this data's own */
+    const int64_t* const* cnt_total;
+    int64_t nnz_total;
 } s3o_data;
 
 typedef struct {
@@ -128,12 +133,14 @@ static double dot(const double* a, const double* b, int n) {
     return s;
 }
 
-/* |Omega^{n,i}| over the train entries, and |Omega_Y^{2,k}| per coupled matrix */
+/* |Omega^{n,i}| over the train entries, and |Omega_Y^{2,k}| per coupled matrix (the larger
+   problem's, when the data is a part of one) */
 static int64_t** tensor_counts(const s3o_data* d) {
     int64_t** c = (int64_t**)malloc(sizeof(int64_t*) * d->N);
     for (int n = 0; n < d->N; ++n) {
         c[n] = (int64_t*)calloc((size_t)d->I[n], sizeof(int64_t));
-        for (int64_t e = 0; e < d->nnz; ++e) c[n][d->idx[(int64_t)n * d->nnz + e]]++;
+        if (d->cnt_total) memcpy(c[n], d->cnt_total[n], sizeof(int64_t) * (size_t)d->I[n]);
+        else for (int64_t e = 0; e < d->nnz; ++e) c[n][d->idx[(int64_t)n * d->nnz + e]]++;
     }
     return c;
 }
@@ -141,10 +148,13 @@ static int64_t** coupled_counts(const s3o_data* d) {
     int64_t** c = (int64_t**)malloc(sizeof(int64_t*) * (d->M > 0 ? d->M : 1));
     for (int m = 0; m < d->M; ++m) {
         c[m] = (int64_t*)calloc((size_t)d->K[m], sizeof(int64_t));
-        for (int64_t b = 0; b < d->ynnz[m]; ++b) c[m][d->yc[m][b]]++;
+        if (d->cnt_total) memcpy(c[m], d->cnt_total[d->N + m], sizeof(int64_t) * (size_t)d->K[m]);
+        else for (int64_t b = 0; b < d->ynnz[m]; ++b) c[m][d->yc[m][b]]++;
     }
     return c;
 }
+/* |Omega| of the problem the regularisers belong to */
+static double omega(const s3o_data* d) { return d->nnz_total > 0 ? (double)d->nnz_total : (double)d->nnz; }
 static void free_counts(int64_t** c, int n) {
     for (int k = 0; k < n; ++k) free(c[k]);
     free(c);
@@ -229,7 +239,7 @@ static void add_tensor_reg(const s3o_data* d, const s3o_params* p, int64_t e,
         for (int k = 0; k < d->J[n]; ++k) gu[n][k] += w * u[k];
     }
     int64_t P = core_size(d->N, d->J);
-    double w = lambda_reg / (double)d->nnz;
+    double w = lambda_reg / omega(d);
     for (int64_t l = 0; l < P; ++l) gG[l] += w * p->G[l];
 }
 
@@ -296,7 +306,7 @@ void s3o_loss(const s3o_data* d, const s3o_params* p, const s3o_hparams* hp, dou
     for (int64_t e = 0; e < d->nnz; ++e) {
         entry_rows(d, p, e, a);
         double err = d->x[e] - tucker_entry(N, d->J, p->G, a);
-        double term = err * err + hp->lambda_reg / (double)d->nnz * G2;
+        double term = err * err + hp->lambda_reg / omega(d) * G2;
         for (int n = 0; n < N; ++n) {
             int64_t i = d->idx[(int64_t)n * d->nnz + e];
             term += hp->lambda_reg * dot(a[n], a[n], d->J[n]) / (double)cnt[n][i];
@@ -436,7 +446,7 @@ double s3o_entry_gradient_opt(const s3o_data* d, const s3o_params* p, const s3o_
         q += J[n];
     }
     for (int64_t l = 0; l < P; ++l)
-        gG[l] = -err * S[l] / p->G[l] + hp->lambda_reg / (double)d->nnz * p->G[l];
+        gG[l] = -err * S[l] / p->G[l] + hp->lambda_reg / omega(d) * p->G[l];
     free(S);
     free_counts(cnt, N);
     return err;

@@ -24,7 +24,8 @@ STATUS_NAMES = {0: "S3_OK", -1: "S3_ERR_ARG", -2: "S3_ERR_INDEX", -3: "S3_ERR_OO
 EXPORTS = ("s3_init", "s3_epoch", "s3_loss", "s3_rmse", "s3_set_test", "s3_predict",
            "s3_gradient", "s3_get_params", "s3_set_params", "s3_get_epoch", "s3_set_epoch",
            "s3_update_values", "s3_info", "s3_hog_config", "s3_profile", "s3_profile_read",
-           "s3_rmse_noalloc", "s3_finalize_qr", "s3_measure_fp32_peak",
+           "s3_rmse_noalloc", "s3_finalize_qr", "s3_measure_fp32_peak", "s3_set_counts",
+           "s3_apply_gradient",
            "s3_last_error", "s3_destroy")
 S3_K_ALL, S3_K_TENSOR_HOG, S3_K_TENSOR_MB, S3_K_TENSOR_GRAD, S3_K_TENSOR_FWD = -1, 0, 1, 2, 3
 
@@ -44,7 +45,8 @@ class s3_hparams(C.Structure):
                 ("lambda_m", C.c_float), ("batch", C.c_int), ("core_scale", C.c_float),
                 ("row_rule", C.c_int), ("hog_tile", C.c_int), ("hog_staleness", C.c_float),
                 ("hog_ctas", C.c_int), ("mb_ctas", C.c_int), ("cp", C.c_int), ("nonneg", C.c_int),
-                ("grad_chunk", C.c_int), ("hog_core_sync", C.c_int)]
+                ("grad_chunk", C.c_int), ("hog_core_sync", C.c_int), ("wait_limit_us", C.c_int),
+                ("device_bytes_cap", C.c_int64)]
 
 
 class S3Error(RuntimeError):
@@ -98,6 +100,8 @@ def load(build_if_missing=True):
                                         C.POINTER(C.c_int64)]
         lib.s3_rmse_noalloc.argtypes = [vp, pp, vp, C.c_int64, C.POINTER(C.c_double)]
         lib.s3_measure_fp32_peak.argtypes = [C.POINTER(C.c_double)] * 3
+        lib.s3_set_counts.argtypes = [vp, pp, C.c_int64]
+        lib.s3_apply_gradient.argtypes = [vp, vp, pp, pp]
         lib.s3_last_error.argtypes = [vp]
         lib.s3_last_error.restype = C.c_char_p
         lib.s3_destroy.argtypes = [vp]

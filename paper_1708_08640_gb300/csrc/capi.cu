@@ -16,9 +16,19 @@
 using namespace s3;
 
 static constexpr size_t kMaxSmem = 227 * 1024;   // dynamic shared memory per CTA on sm_103a
-// default HOGWILD staleness budget for 3-way tensors: tensor entries in flight at once
-// (304 CTAs x 96 entries)
+// default HOGWILD staleness budget for 3-way tensors up to rank 10: tensor entries in flight
+// at once (152 CTAs x 192 entries)
 static constexpr int64_t kHogInflight = 29184;
+
+// The default budget at the largest rank J: kHogInflight up to rank 10, then shrinking as
+// (10 / J)^0.6 (22 029 at rank 16, 19 155 at 20, 14 385 at 32).  Measured on the cfg1 rating
+// tensor against Algorithm 1's test-RMSE curve: at rank 10, 29 184 entries in flight keep the
+// HOGWILD curve within 0.85%; at rank 16 the same number sits 1.2% above it and 21 888 within
+// 0.5% (both forms).
+static int64_t hog_inflight_budget(int jmax) {
+    if (jmax <= 10) return kHogInflight;
+    return (int64_t)std::llround((double)kHogInflight * std::pow(10.0 / (double)jmax, 0.6));
+}
 
 namespace {
 
@@ -45,6 +55,7 @@ struct s3_ctx {
     int cmode[kMaxM] = {};
     int64_t K[kMaxM] = {};
     int64_t nnz = 0, ynnz[kMaxM] = {}, n_union = 0;
+    int64_t nnz_total = 0;          // |Omega| of the whole problem (s3_set_counts), else nnz
     s3_hparams hp{};
     uint64_t seed = 0;
     int64_t epoch = 0;
@@ -53,6 +64,7 @@ struct s3_ctx {
     bool failed = false;
     std::string err;
     std::vector<void*> allocs;
+    int64_t bytes_allocated = 0;    // device memory taken by dalloc (against hp.device_bytes_cap)
     DParams P{};
     float* inv_cnt[kMaxF] = {};
     int64_t hog_grid = 1;
@@ -142,13 +154,25 @@ static void prof_count(s3_ctx* ctx, int family, int64_t entries) {
     ctx->fam[family].entries += entries;
 }
 
+// every device allocation of a context; the cap of hp.device_bytes_cap makes an allocation
+// beyond it fail as if the device were full
 template <typename T>
 static cudaError_t dalloc(s3_ctx* ctx, T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
+    const int64_t bytes = (int64_t)(n * sizeof(T));
+    if (ctx->hp.device_bytes_cap > 0 && ctx->bytes_allocated + bytes > ctx->hp.device_bytes_cap)
+        return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
-    if (e == cudaSuccess) ctx->allocs.push_back(*p);
+    if (e == cudaSuccess) {
+        ctx->allocs.push_back(*p);
+        ctx->bytes_allocated += bytes;
+    }
     return e;
+}
+
+static uint64_t wait_ns(const s3_ctx* ctx) {
+    return ctx->hp.wait_limit_us > 0 ? (uint64_t)ctx->hp.wait_limit_us * 1000ull : 2000000000ull;
 }
 
 template <typename T>
@@ -266,7 +290,10 @@ static cudaError_t to_host(const T* p, int64_t n, int device_ptrs, std::vector<T
 
 static int ensure_red(s3_ctx* ctx, int64_t pairs) {
     if (pairs <= ctx->red_parts_n) return S3_OK;
-    if (ctx->red_parts) cudaFree(ctx->red_parts);
+    if (ctx->red_parts) {
+        cudaFree(ctx->red_parts);
+        ctx->bytes_allocated -= ctx->red_parts_n * 2 * (int64_t)sizeof(float);
+    }
     ctx->allocs.erase(std::remove(ctx->allocs.begin(), ctx->allocs.end(), (void*)ctx->red_parts),
                       ctx->allocs.end());
     CK(dalloc(ctx, &ctx->red_parts, (size_t)pairs * 2));
@@ -301,6 +328,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     ctx->hp = *hp;
     ctx->seed = seed;
     ctx->nnz = train->nnz;
+    ctx->nnz_total = train->nnz;
     ctx->stream = (cudaStream_t)stream;
     int Jmax = 0;
     for (int n = 0; n < N; ++n) {
@@ -319,7 +347,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     if (!(hp->lr0 > 0.f) || !(hp->mu >= 0.f) || !(hp->lambda_reg >= 0.f) || !(hp->lambda_m >= 0.f) ||
         !(hp->core_scale >= 0.f) || hp->batch < 1 || (hp->row_rule != 0 && hp->row_rule != 1) ||
         hp->hog_tile < 0 || hp->hog_ctas < 0 || hp->mb_ctas < 0 || (hp->cp != 0 && hp->cp != 1) ||
-        (hp->nonneg != 0 && hp->nonneg != 1) || hp->grad_chunk < 0 || hp->hog_core_sync < 0)
+        (hp->nonneg != 0 && hp->nonneg != 1) || hp->grad_chunk < 0 || hp->hog_core_sync < 0 ||
+        hp->wait_limit_us < 0 || hp->device_bytes_cap < 0)
         return bail(S3_ERR_ARG, "invalid hyper-parameters");
     for (int m = 0; m < n_coupled; ++m) {
         const s3_coo_matrix& y = Y[m];
@@ -408,8 +437,9 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // two lanes per entry; tiles of up to T / 4 entries take four), T for 4-way (one lane),
     // T = hog_compute_threads.  Default for 3-way tensors: the largest tile (192 entries up
     // to padded rank 16, 128 at 20, 64 at 32, whose core fills most of shared memory) and
-    // about kHogInflight entries in flight (CTAs capped at kHogInflight / tile): the HOGWILD
-    // test-RMSE curve then stays within 1% of Algorithm 1's on the cfg1 workload.
+    // about hog_inflight_budget(largest rank) entries in flight (CTAs capped at budget / tile):
+    // the HOGWILD test-RMSE curve then stays within 1% of Algorithm 1's on the cfg1 workload
+    // at ranks 10 and 16.
     const int64_t hog_t = hog_compute_threads(N, ctx->JP);
     const int64_t tile_max = N == 3 ? hog_t / 2 : hog_t;
     // (S3CMTF-CP runs its own one-thread-per-entry kernel on these tiles: 128 entries on 228
@@ -422,6 +452,9 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // the BF16 form computes at rank 16 or 32 (the tensor cores' granularity), zero-extending
     // the context's layout
     const bool bf16_ok = N == 3 && ctx->JP <= 32;
+    int jmax = 1;
+    for (int n = 0; n < N; ++n) jmax = std::max(jmax, J[n]);
+    const int64_t budget = hog_inflight_budget(jmax);
     ctx->bf_jp = ctx->JP <= 16 ? 16 : (ctx->JP == 20 ? 20 : 32);
     std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb, kShortSeg);
     if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SLOT, hhog);
@@ -438,7 +471,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
                                : 1;
         int64_t cap = (int64_t)per_sm * ctx->num_sms;
         if (hp->hog_ctas > 0) cap = std::min<int64_t>(cap, hp->hog_ctas);
-        else if (N == 3) cap = std::min<int64_t>(cap, std::max<int64_t>(1, kHogInflight / tile));
+        else if (N == 3) cap = std::min<int64_t>(cap, std::max<int64_t>(1, budget / tile));
         ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(cap, hhog.ngroups));
         ctx->hog_per_sm = per_sm;
         ctx->hog_tile = tile;
@@ -450,30 +483,40 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
                                 ? std::max(1, tensor_cp_blocks_per_sm(N, ctx->JP, ctx->cp_smem)) : 1;
             int64_t ccap = (int64_t)cps * ctx->num_sms;
             if (hp->hog_ctas > 0) ccap = std::min<int64_t>(ccap, hp->hog_ctas);
-            else ccap = std::min<int64_t>(ccap, std::max<int64_t>(1, kHogInflight / tile));
+            else ccap = std::min<int64_t>(ccap, std::max<int64_t>(1, budget / tile));
             ctx->hog_grid = std::max<int64_t>(1, std::min<int64_t>(ccap, hhog.ngroups));
             ctx->hog_per_sm = cps;
         }
     }
-    // The BF16 form takes full tiles of 128 entries (the MMA's M) when its shared memory
-    // allows, and as many CTAs as fit (two per SM at rank 16, one above), capped by hog_ctas
-    // and, on 3-way tensors without hog_ctas, by the same budget of entries in flight as the
-    // FP32 form's default (kHogInflight).  Smaller tiles only when a tile's row slots and
-    // coupled entries would not fit.
+    // The BF16 form holds as many entries in flight as the FP32 form (the same lock-free
+    // schedule: the two differ by their arithmetic only).  It takes full tiles of 128 entries
+    // (the MMA's M) on as many CTAs as that makes, when they occupy at least 90% of the SMs;
+    // else smaller tiles (multiples of 16, at least 32) on one CTA per SM.  With hog_ctas
+    // given, that many CTAs of 128-entry tiles.  Smaller tiles also when a tile's row slots
+    // and coupled entries would not fit in shared memory.
     int64_t bf_tile = tensor_hog_bf16_tile();
     if (msg.empty() && bf16_ok) {
         ctx->hog_bf_sync = hp->hog_core_sync > 0 ? hp->hog_core_sync : tensor_hog_bf16_core_sync(ctx->bf_jp);
-        for (int64_t t = tensor_hog_bf16_tile(); t >= 16; t -= 32) {
+        const int64_t full = tensor_hog_bf16_tile();
+        const int64_t inflight = ctx->hog_grid * ctx->hog_tile;
+        int64_t want_ctas = 0, t0 = full;
+        if (hp->hog_ctas > 0) {
+            want_ctas = hp->hog_ctas;
+        } else if (inflight >= full * ctx->num_sms * 9 / 10) {
+            want_ctas = std::max<int64_t>(1, inflight / full);
+        } else {
+            t0 = std::max<int64_t>(32, std::min<int64_t>(full, inflight / ctx->num_sms / 16 * 16));
+            want_ctas = std::max<int64_t>(1, inflight / t0);
+        }
+        for (int64_t t = t0; t >= 16; t -= 16) {
             bf_tile = t;
             hhog_bf = HostGrouping{};
             msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, bf_tile, POS_SLOT, hhog_bf);
             if (!msg.empty()) break;
             const size_t smem = tensor_hog_bf16_smem(ctx->bf_jp, hhog_bf.max_ev, hhog_bf.max_seg, nF);
             const int per_sm = smem <= kMaxSmem ? tensor_hog_bf16_blocks_per_sm(ctx->bf_jp, smem) : 0;
-            if (per_sm >= 1 || t - 32 < 16) {
-                int64_t ctas = (int64_t)std::max(per_sm, 1) * ctx->num_sms;
-                if (hp->hog_ctas > 0) ctas = std::min<int64_t>(ctas, hp->hog_ctas);
-                else ctas = std::min<int64_t>(ctas, std::max<int64_t>(1, kHogInflight / bf_tile));
+            if (per_sm >= 1 || t - 16 < 16) {
+                const int64_t ctas = std::min<int64_t>((int64_t)std::max(per_sm, 1) * ctx->num_sms, want_ctas);
                 ctx->hog_bf_grid = per_sm >= 1 ? ctas : 0;
                 ctx->hog_bf_per_sm = std::max(per_sm, 1);
                 ctx->hog_bf_tile = bf_tile;
@@ -682,6 +725,7 @@ static int enqueue_minibatch(s3_ctx* ctx) {
     L.row_mean = ctx->hp.row_rule == S3_ROW_MEAN;
     L.n_batches = ctx->mb.ngroups;
     L.grid = ctx->mb_grid;
+    L.wait_ns = wait_ns(ctx);
     CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_MB));
     KL(launch_minibatch_epoch(ctx->N, ctx->JP, ctx->P, ctx->mb.d, L, ctx->stream));
@@ -736,7 +780,8 @@ static int enqueue_hogwild_bf16(s3_ctx* ctx) {
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     KL(launch_tensor_hog_bf16(ctx->bf_jp, ctx->P, D.d, D.ngroups, ctx->d_tile_counter, grid,
                               ctx->d_eta, row_mean, ctx->hp.core_scale / (float)grid,
-                              ctx->hog_bf_sync, D.max_ev, D.max_seg, ctx->d_kerr, ctx->stream));
+                              ctx->hog_bf_sync, D.max_ev, D.max_seg, ctx->d_kerr, wait_ns(ctx),
+                              ctx->stream));
     CK(prof_mark(ctx, S3_K_TENSOR_HOG));
     prof_count(ctx, S3_K_TENSOR_HOG, ctx->nnz);
     return S3_OK;
@@ -754,7 +799,15 @@ static int check_params_finite(s3_ctx* ctx, bool* bad) {
     CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->h_flag[1]) {
         ctx->failed = true;
-        return fail(ctx, S3_ERR_CUDA, "a tensor-core wait timed out in the epoch kernel");
+        static const char* sites[] = {"?", "tile start (MMA warp)", "stage-1 buffer free (MMA warp)",
+                                      "Khatri-Rao chunk (MMA warp)", "final commit (MMA warp)",
+                                      "stage-1 buffer full", "Khatri-Rao buffer free", "P3 and core GEMM"};
+        const int code = ctx->h_flag[1];
+        const int site = (code >> 24) & 0x7f;
+        return fail(ctx, S3_ERR_CUDA,
+                    std::string("a bounded wait ran out in the epoch kernel: ") +
+                        (site >= 1 && site <= 7 ? sites[site] : "grid barrier") + ", after " +
+                        std::to_string(code & 0xFFFFFF) + " tiles of its CTA");
     }
     *bad = *ctx->h_flag != 0;
     return S3_OK;
@@ -1015,7 +1068,74 @@ extern "C" int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const*
     KL(launch_add_comp(dG, ctx->grad_comp, pd, ctx->stream));
     for (int F = 0; F < nF; ++F)
         KL(launch_add_comp(outs[F], ctx->grad_comp + off[F], factor_rows(ctx, F) * factor_cols(ctx, F), ctx->stream));
-    KL(launch_core_reg(dG, ctx->P.G, N, ctx->J, ctx->JP, ctx->hp.lambda_reg, ctx->stream));
+    // the core regulariser lambda_reg / |Omega| G of every entry: this context's share of the
+    // whole problem's lambda_reg G
+    KL(launch_core_reg(dG, ctx->P.G, N, ctx->J, ctx->JP,
+                       (float)((double)ctx->hp.lambda_reg * (double)ctx->nnz / (double)ctx->nnz_total),
+                       ctx->stream));
+    return S3_OK;
+}
+
+// ------------------------------------------------------------------ partitioned problems
+extern "C" int s3_set_counts(s3_ctx* ctx, const int64_t* const* counts, int64_t nnz_total) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (!counts || nnz_total < ctx->nnz)
+        return fail(ctx, S3_ERR_ARG, "s3_set_counts: counts missing or nnz_total below this context's entries");
+    const int nF = ctx->N + ctx->M;
+    std::vector<std::vector<float>> inv((size_t)nF);
+    for (int F = 0; F < nF; ++F) {
+        if (!counts[F]) return fail(ctx, S3_ERR_ARG, "s3_set_counts: a count array is NULL");
+        const int64_t rows = factor_rows(ctx, F);
+        std::vector<float> local((size_t)rows);
+        CK(cudaMemcpyAsync(local.data(), ctx->inv_cnt[F], (size_t)rows * sizeof(float), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        inv[(size_t)F].resize((size_t)rows);
+        for (int64_t i = 0; i < rows; ++i) {
+            const int64_t c = counts[F][i];
+            // the context's own count of the row (from 1 / count), which the whole problem's
+            // count must cover
+            const int64_t own = local[(size_t)i] > 0.f ? (int64_t)std::llround(1.0 / (double)local[(size_t)i]) : 0;
+            if (c < own)
+                return fail(ctx, S3_ERR_ARG, "s3_set_counts: factor " + std::to_string(F) + ", row " +
+                                                 std::to_string(i) + ": count below this context's own");
+            inv[(size_t)F][(size_t)i] = c > 0 ? (float)(1.0 / (double)c) : 0.f;
+        }
+    }
+    for (int F = 0; F < nF; ++F)
+        CK(cudaMemcpyAsync(ctx->inv_cnt[F], inv[(size_t)F].data(), inv[(size_t)F].size() * sizeof(float),
+                           cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->nnz_total = nnz_total;
+    ctx->P.inv_nnz = (float)(1.0 / (double)nnz_total);
+    return S3_OK;
+}
+
+extern "C" int s3_apply_gradient(s3_ctx* ctx, const float* dG, const float* const* dU,
+                                 const float* const* dV) {
+    if (!usable(ctx)) return S3_ERR_STATE;
+    if (ctx->hp.row_rule != S3_ROW_SUM)
+        return fail(ctx, S3_ERR_ARG, "s3_apply_gradient: built for the row rule S3_ROW_SUM");
+    if (!dG || !dU || (ctx->M > 0 && !dV)) return fail(ctx, S3_ERR_ARG, "s3_apply_gradient: gradient missing");
+    for (int n = 0; n < ctx->N; ++n)
+        if (!dU[n]) return fail(ctx, S3_ERR_ARG, "s3_apply_gradient: gradient missing");
+    for (int m = 0; m < ctx->M; ++m)
+        if (!dV[m]) return fail(ctx, S3_ERR_ARG, "s3_apply_gradient: gradient missing");
+    const float eta = eta_of(ctx, ctx->epoch);
+    const int nonneg = ctx->hp.nonneg;
+    // the core: -eta core_scale (the mean of the whole epoch's core gradients)
+    KL(launch_core_step(ctx->P.G, dG, ctx->N, ctx->J, ctx->JP,
+                        (float)(-(double)eta * ctx->hp.core_scale / (double)ctx->nnz_total), nonneg,
+                        ctx->hp.cp, ctx->stream));
+    // the rows: -eta (the sum of their gradients)
+    for (int F = 0; F < ctx->N + ctx->M; ++F)
+        KL(launch_rows_step(factor_ptr(ctx, F), ctx->JPR, F < ctx->N ? dU[F] : dV[F - ctx->N],
+                            factor_rows(ctx, F), factor_cols(ctx, F), -eta, nonneg, ctx->stream));
+    ctx->epoch += 1;
+    bool bad = false;
+    int rc;
+    if ((rc = check_params_finite(ctx, &bad)) != S3_OK) return rc;
+    if (bad) return fail(ctx, S3_ERR_DIVERGED, "non-finite parameter after the step");
     return S3_OK;
 }
 

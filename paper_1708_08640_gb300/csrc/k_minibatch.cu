@@ -10,8 +10,9 @@
 //      the CTA partials in CTA order and applies the core step.
 // The slot layout, the sums' order and the CTA partitioning are fixed, so the epoch is
 // deterministic.  Parameters change inside the launch, so every parameter read is a
-// coherent (L2) load.  The barrier waits are bounded: after ~1 s without progress a CTA sets
-// the error flag and leaves, and the others leave at their next barrier.
+// coherent (L2) load.  The barrier waits are bounded (by the context's wait limit, 2 s by
+// default): a CTA whose wait runs out sets the error flag and leaves, and the others leave at
+// their next barrier.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -19,7 +20,11 @@
 
 namespace s3 {
 
-constexpr int kBarrierSpins = 1 << 24;   // x 64 ns sleeps: about one second
+__device__ __forceinline__ uint64_t mb_globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
@@ -28,8 +33,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // sense-free grid barrier: a counter of arrivals and a generation number that the last
-// arriving CTA advances.  Returns false (for the whole CTA) when the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* s_ok) {
+// arriving CTA advances.  Returns false (for the whole CTA) when the wait ran out (after about
+// wait_ns nanoseconds).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int* s_ok, uint64_t wait_ns) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned g = ld_acquire_u32(gen);
@@ -40,11 +46,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, unsigned* gen, int
             __threadfence();
             atomicAdd(gen, 1u);
         } else {
-            int it = 0;
-            while (ld_acquire_u32(gen) == g && it < kBarrierSpins) {
-                __nanosleep(64);
-                ++it;
-            }
+            const uint64_t t0 = mb_globaltimer();
+            while (ld_acquire_u32(gen) == g && mb_globaltimer() - t0 <= wait_ns) __nanosleep(64);
             if (ld_acquire_u32(gen) == g) *s_ok = 0;
         }
         __threadfence();
@@ -66,6 +69,7 @@ struct MbArgs {
     float core_scale;
     int row_mean;
     int64_t n_batches;
+    uint64_t wait_ns;
 };
 
 template <int N, int JP>
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
             }
         }
         if ((int)blockIdx.x < n_part) acc.store(A.core_part + (int64_t)blockIdx.x * Pd, stage);
-        if (!grid_barrier(A.bar_count, A.bar_gen, &s_ok)) break;
+        if (!grid_barrier(A.bar_count, A.bar_gen, &s_ok, A.wait_ns)) break;
         // ------------------------------------------------ phase B: ordered sums and steps
         // each group lists its long segments (more than kShortSeg events) first
         int64_t long_begin[kMaxF + 1], short_begin[kMaxF + 1];
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(kTile) k_mb_epoch(DParams P, DGroup Gr, MbArgs
                 }
             }
         }
-        if (!grid_barrier(A.bar_count, A.bar_gen, &s_ok)) break;
+        if (!grid_barrier(A.bar_count, A.bar_gen, &s_ok, A.wait_ns)) break;
     }
     if (tid == 0 && !s_ok) atomicExch(A.err_flag, 1);
 }
@@ -402,6 +406,7 @@ cudaError_t launch_minibatch_epoch(int N, int JP, const DParams& P, const DGroup
     A.core_scale = L.core_scale;
     A.row_mean = L.row_mean;
     A.n_batches = L.n_batches;
+    A.wait_ns = L.wait_ns;
     DParams Pc = P;
     DGroup Gc = G;
     void* args[] = {&Pc, &Gc, &A};

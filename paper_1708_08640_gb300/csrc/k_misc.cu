@@ -629,4 +629,58 @@ cudaError_t launch_core_reg(float* out, const float* G, int N, const int* J, int
     k_core_reg<<<64, 256, 0, s>>>(out, G, N, Jv, JP, lam);
     return cudaGetLastError();
 }
+
+// A step from a given gradient: rows P[i][j] += alpha * g[i][j] (g dense unpadded, rows of J;
+// P padded to ld), then max(0, .) in the non-negative form
+__global__ void k_rows_step(float* P, int ld, const float* g, int64_t rows, int J, float alpha,
+                            int nonneg) {
+    const int64_t n = rows * J;
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < n;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        float* p = P + (l / J) * ld + (l % J);
+        const float v = fmaf(alpha, g[l], *p);
+        *p = nonneg ? project(v) : v;
+    }
+}
+cudaError_t launch_rows_step(float* P, int ld, const float* g, int64_t rows, int J, float alpha,
+                             int nonneg, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)std::min<int64_t>((rows * J + 255) / 256, 4096);
+    k_rows_step<<<grid, 256, 0, s>>>(P, ld, g, rows, J, alpha, nonneg);
+    return cudaGetLastError();
+}
+
+// the same for the core: G (padded) += alpha * dG (dense unpadded); with cp only the
+// hyper-diagonal is a parameter
+__global__ void k_core_step(float* G, const float* dG, int N, int4 Jv, int JP, float alpha, int nonneg,
+                            int cp) {
+    const int JPR = round4(JP);
+    const int Jn[4] = {Jv.x, Jv.y, Jv.z, Jv.w};
+    int64_t Pd = 1;
+    for (int n = 0; n < N; ++n) Pd *= Jn[n];
+    for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < Pd;
+         l += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = l, q = 0, mul = 1;
+        int jl = 0, j0 = -1;
+        bool diag = true;
+        for (int n = N - 1; n >= 0; --n) {
+            const int j = (int)(r % Jn[n]);
+            r /= Jn[n];
+            if (j0 < 0) j0 = j;
+            diag = diag && j == j0;
+            if (n == N - 1) jl = j;
+            else { q += j * mul; mul *= JP; }
+        }
+        if (cp && !diag) continue;
+        float* p = G + q * JPR + jl;
+        const float v = fmaf(alpha, dG[l], *p);
+        *p = nonneg ? project(v) : v;
+    }
+}
+cudaError_t launch_core_step(float* G, const float* dG, int N, const int* J, int JP, float alpha,
+                             int nonneg, int cp, cudaStream_t s) {
+    int4 Jv = make_int4(J[0], N > 1 ? J[1] : 1, N > 2 ? J[2] : 1, N > 3 ? J[3] : 1);
+    k_core_step<<<64, 256, 0, s>>>(G, dG, N, Jv, JP, alpha, nonneg, cp);
+    return cudaGetLastError();
+}
 }  // namespace s3

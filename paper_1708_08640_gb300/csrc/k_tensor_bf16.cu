@@ -50,10 +50,9 @@ constexpr int kChunk = 128;     // pairs per Khatri-Rao chunk (the M of the core
 constexpr int kTN = 64;         // pairs per stage-1 MMA group (its N)
 constexpr int kNB = 2;          // stage-1 TMEM buffers
 constexpr int kBfThreads = kBfTile + 32;   // four entry warps and the MMA warp
-constexpr int kWaitLimit = 1 << 24;
-// shared memory of at least a third of an SM, so that no more than two CTAs share one (their
-// TMEM allocations of 256 columns then fit together)
-constexpr size_t kBfMinSmem = 80 * 1024;
+// the wait for the MMA warp's last commit before the TMEM is released: never shorter than
+// this, whatever the launch's wait limit
+constexpr uint64_t kEndWaitNs = 2000000000ull;
 
 // JQ: the side of the (j1, j2) pair grid (the rank of modes 1 and 2 the kernel computes
 // at); JK: the last mode's rank, padded to the MMAs' K and N granularity.  (16, 16) and
@@ -88,6 +87,14 @@ struct BfLayout {
     static constexpr int CTAS_PER_SM = TMEM_COLS == 256 ? 2 : 1;
 };
 
+// Dynamic shared memory of at least a third of an SM for layouts that allocate 256 TMEM
+// columns (no more than two CTAs share an SM: their allocations fit together), and of more
+// than half of one for layouts that allocate 512 (one CTA per SM).
+template <int JQ, int JK>
+constexpr size_t bf_min_smem() {
+    return BfLayout<JQ, JK>::TMEM_COLS == 256 ? 80 * 1024 : 116 * 1024;
+}
+
 // mbarriers of the kernel
 enum {
     kBarA3 = 0,      // entry warps: the tile's A3 is in shared memory (or: no more tiles)
@@ -111,6 +118,15 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
 template <int JK>
 __device__ __forceinline__ uint32_t g_off(int pair, int j3) {
     return (uint32_t)((pair / 8) * (JK / 8) * 128 + (j3 / 8) * 128 + (j3 % 8) * 16 + (pair % 8) * 2);
+}
+
+// Where a bounded wait ran out, for the host's message: the first failure of the launch is
+// kept as (site << 24) | (tiles this CTA had finished, at most 2^24 - 1).
+enum { kSiteA3 = 1, kSiteTFree = 2, kSiteKr = 3, kSiteEnd = 4, kSiteTFull = 5, kSiteKrFree = 6,
+       kSiteP3 = 7 };
+__device__ __forceinline__ void record_fail(int* err_flag, int* s_fail, int site, uint32_t tiles) {
+    atomicCAS(err_flag, 0, (site << 24) | (int)(tiles < 0xFFFFFFu ? tiles : 0xFFFFFFu));
+    *s_fail = 1;
 }
 
 // the entry warps' own barrier (the MMA warp runs a separate loop)
@@ -179,7 +195,8 @@ __device__ __forceinline__ void load_core_bf16(const DParams& P, uint8_t* smem_r
 template <int JQ, int JK>
 __global__ void __launch_bounds__(kBfThreads, BfLayout<JQ, JK>::CTAS_PER_SM)
 k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, const float* eta_p,
-                  int row_mean, float core_step_scale, int core_sync, HogSmem H, int* err_flag) {
+                  int row_mean, float core_step_scale, int core_sync, HogSmem H, int* err_flag,
+                  uint64_t wait_ns) {
     using Lt = BfLayout<JQ, JK>;
     constexpr int JPR = JQ;          // slot rows (JQ is a multiple of 4)
     constexpr int NQ = Lt::NQ;
@@ -226,10 +243,14 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     if (warp == kBfTile / 32) {
         // ------------------------------------------------------------ the MMA warp
         if (lane == 0) {
-            uint32_t ph_a3 = 0, nh = 0, nk = 0;
+            uint32_t ph_a3 = 0, nh = 0, nk = 0, tiles = 0;
             bool ok = true;
-            for (;;) {
-                if (!mbar_wait(&s_bar[kBarA3], ph_a3, kWaitLimit)) { ok = false; break; }
+            for (;; ++tiles) {
+                if (!mbar_wait_ns(&s_bar[kBarA3], ph_a3, wait_ns)) {
+                    record_fail(err_flag, &s_fail, kSiteA3, tiles);
+                    ok = false;
+                    break;
+                }
                 ph_a3 ^= 1;
                 if (!s_go) break;
                 const bool fresh = s_fresh != 0;
@@ -239,7 +260,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 for (int h = 0; h < NH && ok; ++h, ++nh) {
                     const uint32_t b = nh % kNB;
                     if (nh >= (uint32_t)kNB &&
-                        !mbar_wait(&s_bar[kBarTFree + b], ((nh / kNB) - 1) & 1, kWaitLimit)) {
+                        !mbar_wait_ns(&s_bar[kBarTFree + b], ((nh / kNB) - 1) & 1, wait_ns)) {
+                        record_fail(err_flag, &s_fail, kSiteTFree, tiles);
                         ok = false;
                         break;
                     }
@@ -258,7 +280,11 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 constexpr uint32_t id_p3 = tc_idesc_bf16(128, JK, 0, 0);
                 constexpr uint32_t id_dg = tc_idesc_bf16(128, JK, 1, 1);
                 for (int c = 0; c < NC; ++c, ++nk) {
-                    if (!mbar_wait(&s_bar[kBarKr], nk & 1, kWaitLimit)) { ok = false; break; }
+                    if (!mbar_wait_ns(&s_bar[kBarKr], nk & 1, wait_ns)) {
+                        record_fail(err_flag, &s_fail, kSiteKr, tiles);
+                        ok = false;
+                        break;
+                    }
                     tc_fence_after();
 #pragma unroll
                     for (int ks = 0; ks < kChunk / 16; ++ks) {
@@ -278,17 +304,17 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 }
                 if (!ok) break;
             }
-            if (!ok) s_fail = 1;
             // nothing this thread issued may still run when the TMEM is released
             tc_commit(&s_bar[kBarEnd]);
-            if (!mbar_wait(&s_bar[kBarEnd], 0, kWaitLimit)) s_fail = 1;
+            if (!mbar_wait_ns(&s_bar[kBarEnd], 0, wait_ns > kEndWaitNs ? wait_ns : kEndWaitNs))
+                record_fail(err_flag, &s_fail, kSiteEnd, tiles);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ the entry warps
         const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
         const float eta = *eta_p;
-        uint32_t ph_p3 = 0, nh = 0, nk = 0;
+        uint32_t ph_p3 = 0, nh = 0, nk = 0, tiles = 0;
         int since_sync = 0, acc_tiles = 0;
         // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
         // starts with its ranges (entries, coupled entries, segments) in shared memory.
@@ -309,6 +335,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 if (lane == 0) mbar_arrive(&s_bar[kBarA3]);
                 break;
             }
+            // whether this is the CTA's last tile, read while s_nxt is the same for every
+            // thread (thread 0 moves it at the tile's end, and warp 0 may get there first)
+            const bool last = s_nxt >= n_tiles;
             // the tile after the next one is claimed now; it is needed only at this one's end
             int claim = 0;
             if (tid == 0) claim = atomicAdd(tile_counter, 1);
@@ -365,12 +394,20 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
 #pragma unroll
             for (int h = 0; h < NH; ++h, ++nh) {
                 const uint32_t b = nh % kNB;
-                if (!mbar_wait(&s_bar[kBarTFull + b], (nh / kNB) & 1, kWaitLimit)) s_fail = 1;
+                bool got = mbar_wait_ns(&s_bar[kBarTFull + b], (nh / kNB) & 1, wait_ns);
+                if (!got) record_fail(err_flag, &s_fail, kSiteTFull, tiles);
+                // after a wait that ran out the warp reads nothing (an MMA may still write)
+                got = __all_sync(0xffffffffu, got);
                 tc_fence_after();
                 uint32_t r[2][32];
-                tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN, r[0]);
-                tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN + 32, r[1]);
-                tmem_wait_ld();
+                if (got) {
+                    tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN, r[0]);
+                    tmem_ld32_nw(lane_base + Lt::COL_T + b * kTN + 32, r[1]);
+                    tmem_wait_ld();
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) { r[0][i] = 0u; r[1][i] = 0u; }
+                }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_bar[kBarTFree + b]);
@@ -449,7 +486,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     kr[i / 2] = pair < NQ ? bf2_bits(__hmul2(b1[pq / JQ], b2[(pq % JQ) / 2])) : 0u;
                 }
                 // the previous chunk's MMAs have read sKR
-                if (nk > 0 && !mbar_wait(&s_bar[kBarKrFree], (nk - 1) & 1, kWaitLimit)) s_fail = 1;
+                if (nk > 0 && !mbar_wait_ns(&s_bar[kBarKrFree], (nk - 1) & 1, wait_ns))
+                    record_fail(err_flag, &s_fail, kSiteKrFree, tiles);
 #pragma unroll
                 for (int kg = 0; kg < kChunk / 8; ++kg) {
                     const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
@@ -460,7 +498,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 if (lane == 0) mbar_arrive(&s_bar[kBarKr]);
             }
             // ---- P3, the mode-3 row gradient, the coupled entries
-            if (!mbar_wait(&s_bar[kBarP3], ph_p3, kWaitLimit)) s_fail = 1;
+            bool p3_ok = mbar_wait_ns(&s_bar[kBarP3], ph_p3, wait_ns);
+            if (!p3_ok) record_fail(err_flag, &s_fail, kSiteP3, tiles);
+            p3_ok = __all_sync(0xffffffffu, p3_ok);
             ph_p3 ^= 1;
             tc_fence_after();
             {
@@ -468,7 +508,12 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
 #pragma unroll
                 for (int hh = 0; hh < JK / 16; ++hh) {
                     float v[16];
-                    tmem_ld16(lane_base + Lt::COL_P3 + 16 * hh, v);
+                    if (p3_ok) {
+                        tmem_ld16(lane_base + Lt::COL_P3 + 16 * hh, v);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                    }
 #pragma unroll
                     for (int i = 0; i < 16; ++i) p3[16 * hh + i] = v[i];
                 }
@@ -496,13 +541,12 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             acc_tiles += nb > 0;
             // ---- the core step of the tiles since the last one, when due (and always at the
             //      CTA's last tile):  G += eta cs / W (sum of tile means - n lambda / |Omega| G)
-            const bool last = s_nxt >= n_tiles;
             if (since_sync >= core_sync || last || failed) {
                 const float sc = eta * core_step_scale;
                 const float rg = eta * core_step_scale * P.lambda_reg * P.inv_nnz * (float)acc_tiles;
                 const __nv_bfloat16* gbf = reinterpret_cast<const __nv_bfloat16*>(smem_raw + Lt::OFF_G);
 #pragma unroll 1
-                for (int c = 0; c < NC; ++c) {
+                for (int c = 0; c < NC && !failed; ++c) {
                     float d[JK];
 #pragma unroll
                     for (int hh = 0; hh < JK / 16; ++hh) {
@@ -551,12 +595,13 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 s_nxt = claim;
                 s_go = s_cur < n_tiles && !failed;
             }
+            ++tiles;
             entry_sync();
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (s_fail && tid == 0) atomicExch(err_flag, 1);
+    if (s_fail && tid == 0) atomicCAS(err_flag, 0, 1);
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, Lt::TMEM_COLS);
 }
@@ -568,12 +613,16 @@ static size_t bf16_fixed_bytes(int JP) {
          : JP == 32 ? BfLayout<32, 32>::OFF_SLOTS : 0;
 }
 
+static size_t bf16_min_smem(int JP) {
+    return JP == 16 ? bf_min_smem<16, 16>() : JP == 20 ? bf_min_smem<20, 32>() : bf_min_smem<32, 32>();
+}
+
 size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* max_segs, int nF) {
     const size_t fixed = bf16_fixed_bytes(JP);
     if (!fixed) return 0;
     const size_t b = hog_smem_floats(JP, max_events, max_segs, nF, nullptr, fixed / sizeof(float)) *
                      sizeof(float);
-    return b < kBfMinSmem ? kBfMinSmem : b;
+    return b < bf16_min_smem(JP) ? bf16_min_smem(JP) : b;
 }
 
 int tensor_hog_bf16_tile() { return kBfTile; }
@@ -600,33 +649,35 @@ template <int JQ, int JK>
 static cudaError_t launch_bf16(const DParams& P, const DGroup& G, int64_t n_tiles, int* tile_counter,
                                int grid, const float* eta, int row_mean, float core_step_scale,
                                int core_sync, const HogSmem& H, size_t smem, int* err_flag,
-                               cudaStream_t s) {
+                               uint64_t wait_ns, cudaStream_t s) {
     cudaError_t e = prep_bf16(k_tensor_hog_bf16<JQ, JK>, smem);
     if (e != cudaSuccess) return e;
     k_tensor_hog_bf16<JQ, JK><<<grid, kBfThreads, smem, s>>>(P, G, n_tiles, tile_counter, eta, row_mean,
-                                                             core_step_scale, core_sync, H, err_flag);
+                                                             core_step_scale, core_sync, H, err_flag,
+                                                             wait_ns);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
                                    float core_step_scale, int core_sync, const int64_t* max_events,
-                                   const int64_t* max_segs, int* err_flag, cudaStream_t s) {
+                                   const int64_t* max_segs, int* err_flag, uint64_t wait_ns,
+                                   cudaStream_t s) {
     const size_t fixed = bf16_fixed_bytes(JP);
     if (!fixed || P.N != 3 || core_sync < 1) return cudaErrorInvalidValue;
     if (n_tiles <= 0) return cudaSuccess;
     HogSmem H{};
     size_t smem = hog_smem_floats(JP, max_events, max_segs, P.N + P.M, &H, fixed / sizeof(float)) *
                   sizeof(float);
-    if (smem < kBfMinSmem) smem = kBfMinSmem;
+    if (smem < bf16_min_smem(JP)) smem = bf16_min_smem(JP);
     if (JP == 16)
         return launch_bf16<16, 16>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
-                                   core_sync, H, smem, err_flag, s);
+                                   core_sync, H, smem, err_flag, wait_ns, s);
     if (JP == 20)
         return launch_bf16<20, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
-                                   core_sync, H, smem, err_flag, s);
+                                   core_sync, H, smem, err_flag, wait_ns, s);
     return launch_bf16<32, 32>(P, G, n_tiles, tile_counter, grid, eta, row_mean, core_step_scale,
-                               core_sync, H, smem, err_flag, s);
+                               core_sync, H, smem, err_flag, wait_ns, s);
 }
 
 // CTAs of the BF16 kernel that fit on one SM with this much dynamic shared memory (at most

@@ -53,7 +53,8 @@ size_t tensor_hog_bf16_smem(int JP, const int64_t* max_events, const int64_t* ma
 cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, int64_t n_tiles,
                                    int* tile_counter, int grid, const float* eta, int row_mean,
                                    float core_step_scale, int core_sync, const int64_t* max_events,
-                                   const int64_t* max_segs, int* err_flag, cudaStream_t s);
+                                   const int64_t* max_segs, int* err_flag, uint64_t wait_ns,
+                                   cudaStream_t s);
 
 // Deterministic minibatch epoch as one cooperative launch of `grid` CTAs (see k_minibatch.cu).
 struct MbLaunch {
@@ -67,6 +68,7 @@ struct MbLaunch {
     int row_mean;
     int64_t n_batches;
     int grid;
+    uint64_t wait_ns;        // bound of a grid-barrier wait
 };
 int minibatch_epoch_grid(int N, int JP, int num_sms);   // co-resident CTAs, 0 if none
 cudaError_t launch_minibatch_epoch(int N, int JP, const DParams& P, const DGroup& G,
@@ -169,6 +171,13 @@ cudaError_t launch_add_comp(float* out, const float* comp, int64_t n, cudaStream
 // dG (dense unpadded) += lam * G (G padded)
 cudaError_t launch_core_reg(float* out, const float* G, int N, const int* J, int JP, float lam,
                             cudaStream_t s);
+// a step from a given gradient: P (rows padded to ld) += alpha * g (dense, rows of J), and the
+// core G (padded) += alpha * dG (dense; cp: the hyper-diagonal only); then max(0, .) with
+// nonneg
+cudaError_t launch_rows_step(float* P, int ld, const float* g, int64_t rows, int J, float alpha,
+                             int nonneg, cudaStream_t s);
+cudaError_t launch_core_step(float* G, const float* dG, int N, const int* J, int JP, float alpha,
+                             int nonneg, int cp, cudaStream_t s);
 // dst[k] = src[idx[k]] (values into the library's layout)
 cudaError_t launch_gather_f32(float* dst, const float* src, const int64_t* idx, int64_t n,
                               cudaStream_t s);

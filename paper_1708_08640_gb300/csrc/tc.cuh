@@ -63,6 +63,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int l
     return done != 0;
 }
 
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for the phase with the given parity, bounded in time: false once about limit_ns
+// nanoseconds have passed without it
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
+    uint32_t done = 0;
+    uint64_t t0 = 0;
+    for (int round = 0;; ++round) {
+        for (int i = 0; i < 64 && !done; ++i)
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+        if (done) return true;
+        const uint64_t now = globaltimer_ns();
+        if (round == 0) t0 = now;
+        else if (now - t0 > limit_ns) return false;
+    }
+}
+
 // one arrival on the mbarrier (release at CTA scope)
 __device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(mbar)) : "memory");

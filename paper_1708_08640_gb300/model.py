@@ -41,7 +41,7 @@ class S3CMTF:
     def __init__(self, dims, J, train_idx, train_val, coupled=(), *, lr0=0.01, mu=0.1,
                  lambda_reg=0.01, lambda_m=1.0, batch=4096, core_scale=1.0, row_rule="sum",
                  hog_tile=0, hog_staleness=0.0, hog_ctas=0, mb_ctas=0, cp=0, nonneg=0,
-                 grad_chunk=0, hog_core_sync=0, seed=0,
+                 grad_chunk=0, hog_core_sync=0, wait_limit_us=0, device_bytes_cap=0, seed=0,
                  order=None,
                  device=None,
                  stream=None):
@@ -76,7 +76,8 @@ class S3CMTF:
         hp = L.s3_hparams(lr0, mu, lambda_reg, lambda_m, int(batch), core_scale,
                           _ROW[row_rule] if isinstance(row_rule, str) else int(row_rule),
                           int(hog_tile), float(hog_staleness), int(hog_ctas), int(mb_ctas),
-                          int(cp), int(nonneg), int(grad_chunk), int(hog_core_sync))
+                          int(cp), int(nonneg), int(grad_chunk), int(hog_core_sync),
+                          int(wait_limit_us), int(device_bytes_cap))
         Jarr = (C.c_int * self.N)(*self.J)
         order_arr = None if order is None else _host(order, np.int64)
         with torch.cuda.device(self.device):
@@ -202,6 +203,24 @@ class S3CMTF:
                                          L.ptr_array([v.data_ptr() for v in dV])))
         self._leave(dG, *dU, *dV, *([] if wd is None else [wd]))
         return dG, dU, dV
+
+    def set_counts(self, counts, nnz_total):
+        """The whole problem's row counts (one int64 array per factor: U^(1..N), then V_m)
+        and |Omega|, for a model that holds one part of it (s3_set_counts)."""
+        arrs = [np.ascontiguousarray(np.asarray(c), dtype=np.int64) for c in counts]
+        self._check(self.lib.s3_set_counts(self.ctx, L.ptr_array([a.ctypes.data for a in arrs]),
+                                           int(nnz_total)))
+
+    def apply_gradient(self, dG, dU, dV):
+        """One minibatch-rule step whose group is the whole epoch, from the whole problem's
+        gradient (device tensors of the parameter shapes; s3_apply_gradient)."""
+        dG = _dev(dG, torch.float32, self.device).contiguous()
+        dU = [_dev(u, torch.float32, self.device).contiguous() for u in dU]
+        dV = [_dev(v, torch.float32, self.device).contiguous() for v in dV]
+        self._enter()
+        self._check(self.lib.s3_apply_gradient(self.ctx, dG.data_ptr(),
+                                               L.ptr_array([u.data_ptr() for u in dU]),
+                                               L.ptr_array([v.data_ptr() for v in dV])))
 
     def get_params(self):
         G, U, V = self._param_buffers()

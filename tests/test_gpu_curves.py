@@ -1,8 +1,9 @@
 """The GPU epochs against the oracle's stored test-RMSE curves on the cfg1 workloads
 (tests/golden/curve_*.json, written by tests/golden/make_golden.py from oracle/ alone):
-the HOGWILD epoch tracks the sequential Algorithm 1 (P = 1) curve within 1% per epoch,
-and the deterministic minibatch epoch reproduces the oracle's minibatch curve; the same two
-checks for the non-negative form (projected SGD, Section 5)."""
+the HOGWILD epoch, in both precision forms, tracks the sequential Algorithm 1 (P = 1) curve
+within 1% per epoch (rank 10, and rank 16 for cfg2), and the deterministic minibatch epoch
+reproduces the oracle's minibatch curve; the same two checks for the non-negative form
+(projected SGD, Section 5)."""
 import hashlib
 import json
 import os
@@ -31,9 +32,10 @@ def fingerprint(p):
     return h.hexdigest()[:16]
 
 
-def gpu_curve(p, rec, mode, **kw):
+def gpu_curve(p, rec, mode, precision="fp32", **kw):
     from paper_1708_08640_gb300.model import S3CMTF
-    hp = dict(rec["hparams"])
+    hp = dict(p.hparams)
+    hp.update(rec["hparams"])
     if rec.get("minibatch"):
         mb = rec["minibatch"]
         hp.update(batch=mb["batch"], core_scale=mb["core_scale"], row_rule="mean" if mb["row_mean"] else "sum")
@@ -42,7 +44,7 @@ def gpu_curve(p, rec, mode, **kw):
     m.set_test(p.test_idx, p.test_val)
     out = []
     for _ in range(rec["epochs"]):
-        m.epoch(mode)
+        m.epoch(mode, precision)
         out.append(m.rmse())
     m.close()
     return np.array(out)
@@ -58,6 +60,37 @@ def test_hogwild_tracks_algorithm1_on_cfg1(cuda_lib, rating_tensor):
     ref = np.array(rec["test_rmse"])
     dev = np.abs(got - ref) / ref
     print("HOGWILD vs Algorithm 1, relative deviation per epoch:", np.round(dev, 5).tolist())
+    assert np.all(dev <= 0.01), dev
+
+
+def test_bf16_hogwild_tracks_algorithm1_on_cfg1(cuda_lib, rating_tensor):
+    """The BF16 tensor-core form of the same epoch (rank 10 computed on the 16 x 16 pair
+    grid, the same 29 184 entries in flight): within 1% of Algorithm 1 after each of 10
+    epochs, like the FP32 form."""
+    rec = golden("cfg1", "sequential")
+    assert fingerprint(rating_tensor) == rec["fingerprint"]
+    got = gpu_curve(rating_tensor, rec, "hogwild", "bf16")
+    ref = np.array(rec["test_rmse"])
+    dev = np.abs(got - ref) / ref
+    print("BF16 HOGWILD vs Algorithm 1, relative deviation per epoch:", np.round(dev, 5).tolist())
+    assert np.all(dev <= 0.01), dev
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_hogwild_tracks_algorithm1_at_rank16_on_cfg1(cuda_lib, rating_tensor, precision):
+    """cfg2's rank: the cfg1 data fitted at J = (16, 16, 16) (core step scale of that rank),
+    the default launch (about 22 000 entries in flight at rank 16), both precision forms:
+    test RMSE within 1% of the oracle's Algorithm 1 curve after each stored epoch."""
+    from paper_1708_08640_gb300 import synth
+    rec = golden("cfg1_j16", "sequential")
+    q = synth.with_rank(rating_tensor, (16, 16, 16))
+    assert rec["rank"] == [16, 16, 16]
+    assert fingerprint(q) == rec["fingerprint"]
+    got = gpu_curve(q, rec, "hogwild", precision)
+    ref = np.array(rec["test_rmse"])
+    dev = np.abs(got - ref) / ref
+    print(f"{precision} HOGWILD vs Algorithm 1 at rank 16, relative deviation per epoch:",
+          np.round((got - ref) / ref, 5).tolist())
     assert np.all(dev <= 0.01), dev
 
 
