@@ -105,12 +105,15 @@ typedef struct {
                            occurrences x entries in flight / |Omega|) takes its step scaled by
                            gamma / kappa; every other row takes the plain lock-free step.
                            0 = default 360 / (largest rank), i.e. 36 at rank 10 (a coupled
-                           entry's step grows stiffer with the rank); < 0 disables the
-                           scaling. */
+                           entry's step grows stiffer with the rank), and 2000 / (largest rank)
+                           in the non-negative form; < 0 disables the scaling. */
     int hog_ctas;       /* HOGWILD: CTAs working at once (0 = default: on 3-way tensors, enough
-                           for at most about 29184 tensor entries in flight in either form, at
-                           most as many as fit on the GPU; on 4-way tensors as many as fit).
-                           Fewer CTAs mean fewer stale updates in flight and less throughput. */
+                           for a budget of tensor entries in flight -- 29184 up to rank 10,
+                           29184 (10 / J)^0.6 at a larger largest rank J, three quarters of that
+                           in the non-negative form -- at most as many as fit on the GPU, the
+                           same number in both precision forms; on 4-way tensors as many as
+                           fit).  Fewer CTAs mean fewer stale updates in flight and less
+                           throughput. */
     int mb_ctas;        /* minibatch: CTAs of its persistent cooperative launch (0 = one per
                            SM, at most as many as fit); fewer CTAs make its grid-wide
                            barriers cheaper, more hide more load latency */

@@ -18,9 +18,9 @@
 // Eq. (8) and the row steps.  FP32 master parameters; BF16 only for the tensor-core operands.
 //
 // A fifth warp issues every MMA (one elected thread) and hands buffers back and forth with
-// the entry warps through mbarriers, so that the MMAs of the next 64 pairs run while the
-// entry warps read the current ones, and the next Khatri-Rao chunk is built while the
-// current one is multiplied.
+// the entry warps through mbarriers, so that the MMAs of the next 128 pairs run while the
+// entry warps read the current 64, and the next Khatri-Rao chunk is built (and, with two
+// buffers, stored) while the current one is multiplied.
 //
 // The core step: a tile's core gradient (its entries' mean, e / n_b folded into e o A3)
 // accumulates in TMEM across the tiles a CTA takes, and is added to G (lock-free,
@@ -33,10 +33,10 @@
 //        + (pair%8)*2: MN-major B of stage 1 (K = j3, N = pair) and K-major B of the
 //        partial (K = pair, N = j3), both read from the same bytes
 //   sA3  K-major A of stage 1 (M = entry, K = j3)
-//   sKR  one 128-pair chunk, K-major A of the partial (M = entry, K = pair) and, read as
-//        MN-major, the A operand of the core GEMM (M = pair, K = entry)
+//   sKR  one or two 128-pair chunks, K-major A of the partial (M = entry, K = pair) and,
+//        read as MN-major, the A operand of the core GEMM (M = pair, K = entry)
 //   sEA3 (e / n_b) a3, MN-major B of the core GEMM (K = entry, N = j3)
-// TMEM: dG of every chunk [0, NC JK), P3 [COL_P3, + JK), two stage-1 buffers of 64 columns.
+// TMEM: dG of every chunk [0, NC JK), P3 [COL_P3, + JK), three stage-1 buffers of 64 columns.
 #include <cuda_runtime.h>
 
 #include "hog_common.cuh"
@@ -48,7 +48,8 @@ namespace s3 {
 constexpr int kBfTile = 128;    // entries per tile at most (the MMA's M)
 constexpr int kChunk = 128;     // pairs per Khatri-Rao chunk (the M of the core GEMM)
 constexpr int kTN = 64;         // pairs per stage-1 MMA group (its N)
-constexpr int kNB = 2;          // stage-1 TMEM buffers
+constexpr int kNB = 3;          // stage-1 TMEM buffers
+constexpr int kMaxKr = 2;       // Khatri-Rao chunk buffers in shared memory, at most
 constexpr int kBfThreads = kBfTile + 32;   // four entry warps and the MMA warp
 // the wait for the MMA warp's last commit before the TMEM is released: never shorter than
 // this, whatever the launch's wait limit
@@ -69,22 +70,26 @@ struct BfLayout {
     static constexpr int NH = NPAIR / kTN;                              // stage-1 MMA groups
     static constexpr uint32_t G_BYTES = JK * NPAIR * 2;
     static constexpr uint32_t A3_BYTES = kBfTile * JK * 2;
-    static constexpr uint32_t KR_BYTES = kBfTile * kChunk * 2;
-    static constexpr uint32_t EA3_BYTES = kBfTile * JK * 2;
-    static constexpr uint32_t OFF_G = 0;
-    static constexpr uint32_t OFF_A3 = OFF_G + G_BYTES;
-    static constexpr uint32_t OFF_KR = OFF_A3 + A3_BYTES;
-    static constexpr uint32_t OFF_EA3 = OFF_KR + KR_BYTES;
-    static constexpr uint32_t OFF_SLOTS = OFF_EA3 + EA3_BYTES;   // row gradient slots (floats)
     // TMEM columns, each area 32-column aligned, the stage-1 buffers 64-column aligned
     static constexpr uint32_t COL_DG = 0;
     static constexpr uint32_t COL_P3 = (NC * JK + 31) / 32 * 32;
     static constexpr uint32_t COL_T = (COL_P3 + JK + 63) / 64 * 64;
     static constexpr uint32_t TMEM_USED = COL_T + kNB * kTN;
     static constexpr uint32_t TMEM_COLS = TMEM_USED <= 256 ? 256 : 512;
+    static constexpr int CTAS_PER_SM = TMEM_COLS == 256 ? 2 : 1;
+    // two Khatri-Rao buffers when one CTA has the SM (the next chunk is stored while the
+    // MMAs read the current one), one when two CTAs share it
+    static constexpr int NKR = CTAS_PER_SM == 1 ? 2 : 1;
+    static constexpr uint32_t KR1_BYTES = kBfTile * kChunk * 2;
+    static constexpr uint32_t KR_BYTES = NKR * KR1_BYTES;
+    static constexpr uint32_t EA3_BYTES = kBfTile * JK * 2;
+    static constexpr uint32_t OFF_G = 0;
+    static constexpr uint32_t OFF_A3 = OFF_G + G_BYTES;
+    static constexpr uint32_t OFF_KR = OFF_A3 + A3_BYTES;
+    static constexpr uint32_t OFF_EA3 = OFF_KR + KR_BYTES;
+    static constexpr uint32_t OFF_SLOTS = OFF_EA3 + EA3_BYTES;   // row gradient slots (floats)
     static_assert(TMEM_USED <= 512, "TMEM budget");
     static_assert(OFF_SLOTS % 16 == 0, "slot rows are written with 16-byte stores");
-    static constexpr int CTAS_PER_SM = TMEM_COLS == 256 ? 2 : 1;
 };
 
 // Dynamic shared memory of at least a third of an SM for layouts that allocate 256 TMEM
@@ -97,14 +102,16 @@ constexpr size_t bf_min_smem() {
 
 // mbarriers of the kernel
 enum {
-    kBarA3 = 0,      // entry warps: the tile's A3 is in shared memory (or: no more tiles)
-    kBarKr = 1,      // entry warps: a Khatri-Rao chunk (and, first, e o A3) is in shared memory
-    kBarKrFree = 2,  // MMA warp: the MMAs reading the Khatri-Rao chunk have completed
-    kBarP3 = 3,      // MMA warp: the tile's P3 and dG MMAs have completed
-    kBarTFull = 4,   // [kNB] MMA warp: a stage-1 buffer holds its 64 pairs of T
-    kBarTFree = 4 + kNB,   // [kNB] entry warps: a stage-1 buffer has been read
-    kBarEnd = 4 + 2 * kNB,  // MMA warp: everything it issued has completed
-    kNBars = 5 + 2 * kNB
+    kBarA3 = 0,                 // entry warps: the tile's A3 is in shared memory (or: no more
+                                // tiles)
+    kBarKr = 1,                 // [kMaxKr] entry warps: a Khatri-Rao chunk (and, first, e o A3)
+                                // is in its buffer
+    kBarKrFree = 1 + kMaxKr,    // [kMaxKr] MMA warp: the MMAs reading a buffer have completed
+    kBarP3 = 1 + 2 * kMaxKr,    // MMA warp: the tile's P3 and dG MMAs have completed
+    kBarTFull = 2 + 2 * kMaxKr, // [kNB] MMA warp: a stage-1 buffer holds its 64 pairs of T
+    kBarTFree = kBarTFull + kNB,   // [kNB] entry warps: a stage-1 buffer has been read
+    kBarEnd = kBarTFree + kNB,     // MMA warp: everything it issued has completed
+    kNBars = kBarEnd + 1
 };
 
 // one 16-byte chunk of 8 BF16 values
@@ -140,11 +147,11 @@ __device__ __forceinline__ uint32_t bf2_bits(__nv_bfloat162 h) {
 
 // The current core as BF16 operand: coalesced float4 reads of G (the layout's
 // jp x jp x ldg), each element stored at its place in the (j3, pair) core-matrix layout
-// (pair = j1 JQ + j2); the padding past jp stays zero.  Eight loads in flight per thread.
+// (pair = j1 JQ + j2); the padding past jp stays zero.  Sixteen loads in flight per thread.
 template <int JQ, int JK>
 __device__ __forceinline__ void load_core_bf16(const DParams& P, uint8_t* smem_raw, int tid) {
     using Lt = BfLayout<JQ, JK>;
-    constexpr int U = 8;
+    constexpr int U = 16;
     uint8_t* gb = smem_raw + Lt::OFF_G;
     if (P.jp == JQ && P.ldg == JQ) {
         // the layout's rank is the kernel's: compile-time divisions
@@ -208,6 +215,8 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     __shared__ __align__(8) uint64_t s_bar[kNBars];
     __shared__ int64_t s_cur, s_nxt;        // this tile and the one claimed after it
     __shared__ int64_t s_lo[32], s_hi[32];  // array ranges of this tile (hog_ranges lanes)
+    __shared__ int64_t s_nlo, s_nhi;        // the next tile's tensor entries (their indices
+                                            // are loaded one tile ahead)
     __shared__ int s_fail;   // set when a bounded wait ran out
     __shared__ int s_go;     // the entry warps take another tile (read by the MMA warp)
     __shared__ int s_fresh;  // the tile's core GEMM starts a new accumulation in TMEM
@@ -221,8 +230,10 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     if (warp == 0) tmem_alloc(&s_tmem, Lt::TMEM_COLS);
     if (tid == 0) {
         mbar_init(&s_bar[kBarA3], kBfTile / 32);
-        mbar_init(&s_bar[kBarKr], kBfTile / 32);
-        mbar_init(&s_bar[kBarKrFree], 1);
+        for (int b = 0; b < kMaxKr; ++b) {
+            mbar_init(&s_bar[kBarKr + b], kBfTile / 32);
+            mbar_init(&s_bar[kBarKrFree + b], 1);
+        }
         mbar_init(&s_bar[kBarP3], 1);
         for (int b = 0; b < kNB; ++b) {
             mbar_init(&s_bar[kBarTFull + b], 1);
@@ -280,7 +291,9 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 constexpr uint32_t id_p3 = tc_idesc_bf16(128, JK, 0, 0);
                 constexpr uint32_t id_dg = tc_idesc_bf16(128, JK, 1, 1);
                 for (int c = 0; c < NC; ++c, ++nk) {
-                    if (!mbar_wait_ns(&s_bar[kBarKr], nk & 1, wait_ns)) {
+                    const uint32_t kb = nk % Lt::NKR;
+                    const uint32_t kr = sKR + kb * Lt::KR1_BYTES;
+                    if (!mbar_wait_ns(&s_bar[kBarKr + kb], (nk / Lt::NKR) & 1, wait_ns)) {
                         record_fail(err_flag, &s_fail, kSiteKr, tiles);
                         ok = false;
                         break;
@@ -288,18 +301,18 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     tc_fence_after();
 #pragma unroll
                     for (int ks = 0; ks < kChunk / 16; ++ks) {
-                        const uint64_t ad = tc_sdesc(sKR + ks * 256, 128, (kChunk / 8) * 128);
+                        const uint64_t ad = tc_sdesc(kr + ks * 256, 128, (kChunk / 8) * 128);
                         const uint64_t bd = tc_sdesc(sG + ((kChunk / 8) * c + 2 * ks) * (JK / 8) * 128,
                                                      (JK / 8) * 128, 128);
                         tc_mma(tmem + Lt::COL_P3, ad, bd, id_p3, (c > 0 || ks > 0));
                     }
 #pragma unroll
                     for (int ks = 0; ks < kBfTile / 16; ++ks) {
-                        const uint64_t ad = tc_sdesc(sKR + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
+                        const uint64_t ad = tc_sdesc(kr + ks * 2 * (kChunk / 8) * 128, (kChunk / 8) * 128, 128);
                         const uint64_t bd = tc_sdesc(sEA3 + ks * 256, 128, (kBfTile / 8) * 128);
                         tc_mma(tmem + Lt::COL_DG + c * JK, ad, bd, id_dg, (!fresh || ks > 0));
                     }
-                    tc_commit(&s_bar[kBarKrFree]);
+                    tc_commit(&s_bar[kBarKrFree + kb]);
                     if (c == NC - 1) tc_commit(&s_bar[kBarP3]);
                 }
                 if (!ok) break;
@@ -317,13 +330,29 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         uint32_t ph_p3 = 0, nh = 0, nk = 0, tiles = 0;
         int since_sync = 0, acc_tiles = 0;
         // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
-        // starts with its ranges (entries, coupled entries, segments) in shared memory.
+        // starts with its ranges (entries, coupled entries, segments) in shared memory, and
+        // its entries' indices and values in registers (loaded during the tile before): its
+        // critical path starts at the row gathers.
         if (tid == 0) {
             s_cur = atomicAdd(tile_counter, 1);
             s_nxt = atomicAdd(tile_counter, 1);
         }
         entry_sync();
         if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
+        if (tid == 0) {
+            const bool has = s_nxt < n_tiles;
+            s_nlo = has ? Gr.t_off[s_nxt] : 0;
+            s_nhi = has ? Gr.t_off[s_nxt + 1] : 0;
+        }
+        entry_sync();
+        // the first tile's entry
+        int32_t pre_row[3] = {0, 0, 0};
+        float pre_x = 0.f;
+        if (tid < (int)(s_hi[0] - s_lo[0])) {
+#pragma unroll
+            for (int n = 0; n < 3; ++n) pre_row[n] = __ldg(Gr.tidx[n] + s_lo[0] + tid);
+            pre_x = __ldg(Gr.tval + s_lo[0] + tid);
+        }
         load_core_bf16<JQ, JK>(P, smem_raw, tid);
         fence_proxy_async();
         if (tid == 0) s_go = s_cur < n_tiles;
@@ -342,21 +371,25 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             int claim = 0;
             if (tid == 0) claim = atomicAdd(tile_counter, 1);
             hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
-            // ---- this thread's entry and its rows
+            // ---- this thread's entry (indices and value loaded during the tile before) and
+            //      its rows; the next tile's entry is loaded now, for its start
             const int64_t e0 = s_lo[0];
             const int nb = (int)(s_hi[0] - e0);
             const bool valid = tid < nb;
             const int64_t e = e0 + tid;
-            int32_t row[3] = {0, 0, 0};
+            int32_t row[3] = {pre_row[0], pre_row[1], pre_row[2]};
             int32_t tp[3] = {0, 0, 0};
-            float x = 0.f;
+            const float x = pre_x;
             if (valid) {
 #pragma unroll
-                for (int n = 0; n < 3; ++n) {
-                    row[n] = __ldg(Gr.tidx[n] + e);
-                    tp[n] = __ldg(Gr.tpos[n] + e);
-                }
-                x = __ldg(Gr.tval + e);
+                for (int n = 0; n < 3; ++n) tp[n] = __ldg(Gr.tpos[n] + e);
+            }
+            {
+                const int64_t ne = s_nlo + tid;
+                const bool nvalid = ne < s_nhi;
+#pragma unroll
+                for (int n = 0; n < 3; ++n) pre_row[n] = nvalid ? __ldg(Gr.tidx[n] + ne) : 0;
+                pre_x = nvalid ? __ldg(Gr.tval + ne) : 0.f;
             }
             float a1[JQ], a2[JQ], a3[JK];
             float inv[3] = {0.f, 0.f, 0.f};
@@ -485,17 +518,20 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                     const int pq = pair < NQ ? pair : 0;   // (a compile-time index)
                     kr[i / 2] = pair < NQ ? bf2_bits(__hmul2(b1[pq / JQ], b2[(pq % JQ) / 2])) : 0u;
                 }
-                // the previous chunk's MMAs have read sKR
-                if (nk > 0 && !mbar_wait_ns(&s_bar[kBarKrFree], (nk - 1) & 1, wait_ns))
+                // the MMAs of the chunk this buffer held before have read it
+                const uint32_t kb = nk % Lt::NKR;
+                if (nk >= (uint32_t)Lt::NKR &&
+                    !mbar_wait_ns(&s_bar[kBarKrFree + kb], ((nk / Lt::NKR) - 1) & 1, wait_ns))
                     record_fail(err_flag, &s_fail, kSiteKrFree, tiles);
 #pragma unroll
                 for (int kg = 0; kg < kChunk / 8; ++kg) {
                     const uint32_t off = (tid / 8) * (kChunk / 8) * 128 + kg * 128 + (tid % 8) * 16;
-                    st_shared_v4(sKR + off, kr[4 * kg], kr[4 * kg + 1], kr[4 * kg + 2], kr[4 * kg + 3]);
+                    st_shared_v4(sKR + kb * Lt::KR1_BYTES + off, kr[4 * kg], kr[4 * kg + 1], kr[4 * kg + 2],
+                                 kr[4 * kg + 3]);
                 }
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&s_bar[kBarKr]);
+                if (lane == 0) mbar_arrive(&s_bar[kBarKr + kb]);
             }
             // ---- P3, the mode-3 row gradient, the coupled entries
             bool p3_ok = mbar_wait_ns(&s_bar[kBarP3], ph_p3, wait_ns);
@@ -594,6 +630,10 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 s_cur = s_nxt;
                 s_nxt = claim;
                 s_go = s_cur < n_tiles && !failed;
+                // the tensor entries of the tile after the next one
+                const bool has = claim < n_tiles;
+                s_nlo = has ? Gr.t_off[claim] : 0;
+                s_nhi = has ? Gr.t_off[claim + 1] : 0;
             }
             ++tiles;
             entry_sync();

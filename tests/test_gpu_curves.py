@@ -107,12 +107,11 @@ def test_minibatch_reproduces_oracle_curve_on_cfg1(cuda_lib, rating_tensor):
 
 
 def test_nonneg_hogwild_tracks_projected_algorithm1_on_cfg1(cuda_lib, rating_tensor):
-    """The non-negative form (projected SGD, Section 5) on cfg1, J = 10, default launch:
-    the HOGWILD test RMSE after each of 10 epochs within 4% of the oracle's projected
-    Algorithm 1 curve.  Measured: at most 3.3% above it (the plain form: 0.85%); with 29 184
-    entries in flight the projected steps lag the sequential ones more than the plain steps
-    do.  The kernels' arithmetic is pinned separately: one tile is exactly the oracle's
-    projected group step, and the minibatch form reproduces the oracle's projected curve."""
+    """The non-negative form (projected SGD, Section 5) on cfg1, J = 10, with this form's
+    default launch (21 888 entries in flight, hot-row damping threshold 200): the HOGWILD
+    test RMSE after each of 10 epochs within 1% of the oracle's projected Algorithm 1 curve.
+    The kernels' arithmetic is pinned separately: one tile is exactly the oracle's projected
+    group step, and the minibatch form reproduces the oracle's projected curve."""
     rec = golden("cfg1", "sequential_nonneg")
     assert rec["hparams"].get("nonneg") == 1
     assert fingerprint(rating_tensor) == rec["fingerprint"]
@@ -121,7 +120,7 @@ def test_nonneg_hogwild_tracks_projected_algorithm1_on_cfg1(cuda_lib, rating_ten
     dev = np.abs(got - ref) / ref
     print("non-negative HOGWILD vs projected Algorithm 1, relative deviation per epoch:",
           np.round((got - ref) / ref, 5).tolist())
-    assert np.all(dev <= 0.04), dev
+    assert np.all(dev <= 0.01), dev
 
 
 def test_nonneg_minibatch_reproduces_oracle_curve_on_cfg1(cuda_lib, rating_tensor):
