@@ -167,66 +167,36 @@ __device__ __forceinline__ void hog_coupled_one(const DParams& P, float* smem, c
 // order, then one vector atomic, step = -eta * (step scale of the row) * (sum or mean of the
 // row's gradients in the tile).  Slot rows hold JPR floats; global rows P.ld <= JPR, whose
 // P.ld / 4 quads are written.  Threads first, first + stride, ... take the (segment, quad)
-// items of all factors in one sequence, U items at a time (their table and slot loads in
-// flight together; U = 1 for kernels short of registers).
-template <int JPR, int QD, int U>
-__device__ __forceinline__ void hog_flush_items(const DParams& P, const float* smem, const HogSmem& H,
-                                                float eta, int row_mean, int first, int stride, int nq) {
+// items.
+template <int JPR>
+__device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, const HogSmem& H,
+                                          float eta, int row_mean, int first, int stride) {
     constexpr int SS = slot_stride(JPR);
     const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
-    const int q_of = QD > 0 ? QD : nq;   // quads per row (a compile-time count when known)
-    int total = 0;
-    for (int F = 0; F < H.nF; ++F) total += cnts[F] * q_of;
-    for (int l0 = first; l0 < total; l0 += U * stride) {
-        int4 sg[U];
-        int fq[U], qq[U];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int l = l0 + u * stride;
-            ok[u] = l < total;
-            // the item's factor: walk the factors' item counts (shared-memory broadcasts)
-            int F = 0, fb = 0;
-            while (F + 1 < H.nF && l >= fb + cnts[F] * q_of) {
-                fb += cnts[F] * q_of;
-                ++F;
+    const int nq = P.ld / 4;
+    for (int F = 0; F < H.nF; ++F) {
+        const int nseg = cnts[F];
+        const float* sa = smem + H.off[F];
+        const int4* tab = reinterpret_cast<const int4*>(smem + H.toff[F]);
+        float* base = F < P.N ? P.U[F] : P.V[F - P.N];
+        for (int l = first; l < nseg * nq; l += stride) {
+            const int s = l / nq, q = l % nq;
+            const int4 sg = tab[s];   // row, first slot, events, step scale
+            const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
+            float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
+            for (int k = 1; k < cnt; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(sa + (st + k) * SS + 4 * q);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
             }
-            const int li = l - fb;
-            const int sidx = li / q_of;
-            qq[u] = li - sidx * q_of;
-            fq[u] = F;
-            sg[u] = ok[u] ? reinterpret_cast<const int4*>(smem + H.toff[F])[sidx] : make_int4(0, 0, 0, 0);
-        }
-        float4 acc[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            acc[u] = ok[u] ? *reinterpret_cast<const float4*>(smem + H.off[fq[u]] + sg[u].y * SS + 4 * qq[u])
-                           : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!ok[u]) continue;
-            const float* src = smem + H.off[fq[u]] + sg[u].y * SS + 4 * qq[u];
-            for (int k = 1; k < sg[u].z; ++k) {
-                const float4 v = *reinterpret_cast<const float4*>(src + k * SS);
-                acc[u].x += v.x;
-                acc[u].y += v.y;
-                acc[u].z += v.z;
-                acc[u].w += v.w;
-            }
-            const float sc = -eta * __int_as_float(sg[u].w) / (row_mean ? (float)sg[u].z : 1.f);
-            const int F = fq[u];
-            float* dst = (F < P.N ? P.U[F] : P.V[F - P.N]) + (int64_t)sg[u].x * P.ld + 4 * qq[u];
-            red_add_v4(dst, sc * acc[u].x, sc * acc[u].y, sc * acc[u].z, sc * acc[u].w);
+            const float sc = -eta * __int_as_float(sg.w) / (row_mean ? (float)cnt : 1.f);
+            float* dst = base + (int64_t)rr * P.ld + 4 * q;
+            red_add_v4(dst, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
             if (P.nonneg) red_proj_v4(dst);
         }
     }
-}
-
-template <int JPR, int U = 4>
-__device__ __forceinline__ void hog_flush(const DParams& P, const float* smem, const HogSmem& H,
-                                          float eta, int row_mean, int first, int stride) {
-    if (P.ld == JPR) hog_flush_items<JPR, JPR / 4, U>(P, smem, H, eta, row_mean, first, stride, JPR / 4);
-    else hog_flush_items<JPR, 0, U>(P, smem, H, eta, row_mean, first, stride, P.ld / 4);
 }
 
 // The prefetch warp's part.  Its lanes hold the ranges of one tile: lane 0 its tensor

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
         // s_lo / s_hi / s_nxt past the barrier above until the one below)
         int64_t lo = 0, hi = 0;
         if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
-        hog_flush<JPR, 1>(P, smem, H, eta, row_mean, threadIdx.x, blockDim.x);
+        hog_flush<JPR>(P, smem, H, eta, row_mean, threadIdx.x, blockDim.x);
         __syncwarp();   // warp 0's lanes have read s_nxt before thread 0 moves it
         if (tid < 32) {
             s_lo[tid] = lo;

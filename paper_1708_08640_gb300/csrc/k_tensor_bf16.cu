@@ -215,8 +215,6 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
     __shared__ __align__(8) uint64_t s_bar[kNBars];
     __shared__ int64_t s_cur, s_nxt;        // this tile and the one claimed after it
     __shared__ int64_t s_lo[32], s_hi[32];  // array ranges of this tile (hog_ranges lanes)
-    __shared__ int64_t s_nlo, s_nhi;        // the next tile's tensor entries (their indices
-                                            // are loaded one tile ahead)
     __shared__ int s_fail;   // set when a bounded wait ran out
     __shared__ int s_go;     // the entry warps take another tile (read by the MMA warp)
     __shared__ int s_fresh;  // the tile's core GEMM starts a new accumulation in TMEM
@@ -330,29 +328,13 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
         uint32_t ph_p3 = 0, nh = 0, nk = 0, tiles = 0;
         int since_sync = 0, acc_tiles = 0;
         // Tiles are claimed two ahead and their array ranges read one ahead, so that a tile
-        // starts with its ranges (entries, coupled entries, segments) in shared memory, and
-        // its entries' indices and values in registers (loaded during the tile before): its
-        // critical path starts at the row gathers.
+        // starts with its ranges (entries, coupled entries, segments) in shared memory.
         if (tid == 0) {
             s_cur = atomicAdd(tile_counter, 1);
             s_nxt = atomicAdd(tile_counter, 1);
         }
         entry_sync();
         if (tid < 32) hog_ranges(P, Gr, s_cur, n_tiles, H, tid, s_lo[tid], s_hi[tid]);
-        if (tid == 0) {
-            const bool has = s_nxt < n_tiles;
-            s_nlo = has ? Gr.t_off[s_nxt] : 0;
-            s_nhi = has ? Gr.t_off[s_nxt + 1] : 0;
-        }
-        entry_sync();
-        // the first tile's entry
-        int32_t pre_row[3] = {0, 0, 0};
-        float pre_x = 0.f;
-        if (tid < (int)(s_hi[0] - s_lo[0])) {
-#pragma unroll
-            for (int n = 0; n < 3; ++n) pre_row[n] = __ldg(Gr.tidx[n] + s_lo[0] + tid);
-            pre_x = __ldg(Gr.tval + s_lo[0] + tid);
-        }
         load_core_bf16<JQ, JK>(P, smem_raw, tid);
         fence_proxy_async();
         if (tid == 0) s_go = s_cur < n_tiles;
@@ -371,25 +353,21 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             int claim = 0;
             if (tid == 0) claim = atomicAdd(tile_counter, 1);
             hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kBfTile);
-            // ---- this thread's entry (indices and value loaded during the tile before) and
-            //      its rows; the next tile's entry is loaded now, for its start
+            // ---- this thread's entry and its rows
             const int64_t e0 = s_lo[0];
             const int nb = (int)(s_hi[0] - e0);
             const bool valid = tid < nb;
             const int64_t e = e0 + tid;
-            int32_t row[3] = {pre_row[0], pre_row[1], pre_row[2]};
+            int32_t row[3] = {0, 0, 0};
             int32_t tp[3] = {0, 0, 0};
-            const float x = pre_x;
+            float x = 0.f;
             if (valid) {
 #pragma unroll
-                for (int n = 0; n < 3; ++n) tp[n] = __ldg(Gr.tpos[n] + e);
-            }
-            {
-                const int64_t ne = s_nlo + tid;
-                const bool nvalid = ne < s_nhi;
-#pragma unroll
-                for (int n = 0; n < 3; ++n) pre_row[n] = nvalid ? __ldg(Gr.tidx[n] + ne) : 0;
-                pre_x = nvalid ? __ldg(Gr.tval + ne) : 0.f;
+                for (int n = 0; n < 3; ++n) {
+                    row[n] = __ldg(Gr.tidx[n] + e);
+                    tp[n] = __ldg(Gr.tpos[n] + e);
+                }
+                x = __ldg(Gr.tval + e);
             }
             float a1[JQ], a2[JQ], a3[JK];
             float inv[3] = {0.f, 0.f, 0.f};
@@ -630,10 +608,6 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
                 s_cur = s_nxt;
                 s_nxt = claim;
                 s_go = s_cur < n_tiles && !failed;
-                // the tensor entries of the tile after the next one
-                const bool has = claim < n_tiles;
-                s_nlo = has ? Gr.t_off[claim] : 0;
-                s_nhi = has ? Gr.t_off[claim + 1] : 0;
             }
             ++tiles;
             entry_sync();
