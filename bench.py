@@ -56,12 +56,16 @@ def fp32_peak():
     return _FP32_PEAK["peak"], _FP32_PEAK["source"]
 # the sources of the FP32 HOGWILD kernel: a committed DRAM-traffic figure counts only while
 # their hash is the one it was captured on
-KERNEL_SOURCES = ["paper_1708_08640_gb300/csrc/tensor_hog.cuh",
-                  "paper_1708_08640_gb300/csrc/k_tensor_hog2.cu",
-                  "paper_1708_08640_gb300/csrc/hog_common.cuh",
-                  "paper_1708_08640_gb300/csrc/tensor_fp32.cuh",
-                  "paper_1708_08640_gb300/csrc/common.cuh",
-                  "paper_1708_08640_gb300/csrc/kernels.h"]
+_CS = "paper_1708_08640_gb300/csrc/"
+_BASE = [_CS + "common.cuh", _CS + "kernels.h", _CS + "tensor_fp32.cuh"]
+# the source files each profiled kernel is compiled from (its own file and every header)
+KERNEL_SOURCES = {
+    "k_tensor_hog": [_CS + "k_tensor_hog2.cu", _CS + "tensor_hog.cuh", _CS + "hog_common.cuh"] + _BASE,
+    "k_tensor_hog_bf16": [_CS + "k_tensor_bf16.cu", _CS + "tc.cuh", _CS + "hog_common.cuh"] + _BASE,
+    "k_mb_epoch": [_CS + "k_minibatch.cu"] + _BASE,
+    "k_cp_hog": [_CS + "k_cp.cu", _CS + "hog_common.cuh"] + _BASE,
+    "k_tensor_contrib": [_CS + "k_tensor.cu", _CS + "tensor_hog.cuh", _CS + "hog_common.cuh"] + _BASE,
+}
 
 
 def parse():
@@ -80,9 +84,16 @@ def parse():
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32",
                     help="the step's precision form (bf16: HOGWILD mode, 3-way tensors)")
     ap.add_argument("--cpu-sample", type=int, default=600_000,
-                    help="items of the visiting order the CPU oracle baseline processes")
+                    help="items of the visiting order the CPU oracle baseline processes "
+                         "(0: no CPU baseline, e.g. under a profiler)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the gradient-pass and minibatch side measurements")
+    ap.add_argument("--rank", type=int, default=0,
+                    help="run the workload at rank J in every mode instead of its own "
+                         "(rating workloads, e.g. --workload cfg1_small --rank 32)")
+    ap.add_argument("--variant", choices=["plain", "cp", "nonneg"], default="plain",
+                    help="the step's method: plain S3CMTF-TUCKER, S3CMTF-CP (hyper-diagonal "
+                         "core) or the non-negative form (projected SGD)")
     return ap.parse_args()
 
 
@@ -160,9 +171,11 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-def source_sha():
+def source_sha(kernel="k_tensor_hog"):
+    """A digest of the sources `kernel` is compiled from: a committed DRAM figure is used only
+    while it matches."""
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:12]
 
@@ -173,7 +186,9 @@ def committed_traffic(kernel, workload):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = source_sha()
+    if kernel not in KERNEL_SOURCES:
+        return None
+    sha = source_sha(kernel)
     for line in open(path):
         f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
         if f.get("kernel") == kernel and f.get("workload") == workload and f.get("sha") == sha:
@@ -202,6 +217,57 @@ def cpu_baseline(p, sample, order):
     return {"value": sample / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {sample} items of the {p.name} visiting order, one sequential "
                       f"SGD pass (Algorithm 1, P=1), FP64, {dt:.1f} s"}
+
+
+def _part_gradient(args):
+    """One worker of the multi-core CPU baseline: the FP64 oracle's gradient of one mode-1
+    part of a problem, with the whole problem's counts (the partition's rule)."""
+    import oracle
+    from paper_1708_08640_gb300 import partition
+    q, world, rank, hp, params = args
+    part, _ = partition.mode1_part(q, world, rank)
+    counts, nnz_total = partition.whole_counts(q)
+    o = oracle.Oracle(part, counts=counts, nnz_total=nnz_total, **hp)
+    o.set_params(*params)
+    return o.full_gradient()
+
+
+def cpu_baseline_multicore(p, sample, reps=2):
+    """The FP64 oracle on every host core: the minibatch rule with one batch per pass over a
+    bounded sample (the first `sample` tensor entries and a proportional share of each
+    coupled matrix), each core computing the gradient of one mode-1 part with the oracle as
+    it stands, the parts summed in a fixed order and one step taken (the multi-GPU
+    partition's rule, on CPU processes).  Items per second of the pass."""
+    import multiprocessing as mp
+
+    from paper_1708_08640_gb300 import partition
+    cores = max(1, os.cpu_count() or 1)
+    frac = sample / max(p.nnz, 1)
+    q = sub_problem(p, min(sample, p.nnz), max(1, int(round(frac * (p.coupled[0].nnz if p.coupled else 0)))))
+    hp = {k: v for k, v in p.hparams.items() if k in ("lr0", "mu", "lambda_reg", "lambda_m", "core_scale")}
+    params = synth.init_params(q, 1)
+    items = q.nnz + sum(c.nnz for c in q.coupled)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_part_gradient, [(q, cores, r, hp, params) for r in range(cores)])   # warm-up
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            parts = pool.map(_part_gradient, [(q, cores, r, hp, params) for r in range(cores)])
+            gG = sum(g[0] for g in parts)                       # parts added in rank order
+            G, U, V = params
+            eta = hp["lr0"]
+            G1 = G - eta * hp["core_scale"] * gG / q.nnz
+            U1 = [u - eta * sum(g[1][n] for g in parts) for n, u in enumerate(U)]
+            V1 = [v - eta * sum(g[2][m] for g in parts) for m, v in enumerate(V)]
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+    del G1, U1, V1
+    return {"value": items / best, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {q.nnz} tensor entries and {q.n_union - q.nnz} coupled entries of "
+                      f"{p.name}: one minibatch-rule pass with a single batch (the mode-1 partition "
+                      f"over {cores} processes, FP64 oracle gradients summed in a fixed order, "
+                      f"one step), best of {reps}, {best:.1f} s"}
 
 
 def workload_desc(p, mode, precision="fp32"):
@@ -437,11 +503,31 @@ def gradient_pass(p, stream, steps=3):
     fpk, fsrc = fp32_peak()
     achieved = fpe * ke.value / (kms.value / 1000.0) / 1e12 if kms.value > 0 else None
     return {"workload": f"{p.name}: {p.recipe}; J={p.J}", "ms": ms, "bytes": gb,
-            "GB/s": gb / (ms / 1000.0) / 1e9, "chunks": -(-p.n_union // (1 << 20)),
+            "GB/s": gb / (ms / 1000.0) / 1e9, "chunks": -(-p.n_union // (1 << 22)),
             "roofline": {"bound": "alu", "kernel": "k_tensor_contrib", "achieved": achieved,
                          "peak": fpk, "unit": "TFLOP/s", "frac": achieved / fpk if achieved else None,
                          "kernel_ms_per_pass": kms.value / steps, "flops_per_entry": fpe,
                          "share_of_pass": (kms.value / steps) / ms, "peak_source": fsrc}}
+
+
+def cp_bytes(p):
+    """Algorithmic DRAM bytes of one S3CMTF-CP HOGWILD epoch: COO (4N + 4 B) and slot
+    positions (4N B) per tensor entry, COO and positions (20 B) per coupled entry, and each
+    touched row read and written once."""
+    J = p.J[0]
+    rows = sum(int(np.unique(p.train_idx[n]).shape[0]) for n in range(p.N))
+    rows += sum(int(np.unique(c.cols).shape[0]) for c in p.coupled)
+    ld = 4 * ((J + 3) // 4)
+    return p.nnz * (8 * p.N + 4) + sum(c.nnz * 20 for c in p.coupled) + rows * ld * 4 * 2
+
+
+def cp_params(p):
+    """The seeded start of S3CMTF-CP: the usual factors and a hyper-diagonal N(0,1) core."""
+    G, U, V = synth.init_params(p, 1)
+    J = p.J[0]
+    G = np.zeros(p.J)
+    G[(np.arange(J),) * p.N] = np.random.default_rng(1).normal(size=J)
+    return G, U, V
 
 
 def cp_hogwild(p, order, stream, epochs=3):
@@ -455,13 +541,8 @@ def cp_hogwild(p, order, stream, epochs=3):
 
     from paper_1708_08640_gb300 import _lib as L
     from paper_1708_08640_gb300.model import S3CMTF
-    G, U, V = synth.init_params(p, 1)
-    J = p.J[0]
-    lam = np.random.default_rng(1).normal(size=J)
-    G = np.zeros(p.J)
-    G[(np.arange(J),) * p.N] = lam
     m = S3CMTF.from_problem(p, order=order, stream=stream, cp=1)
-    m.set_params(G, U, V)
+    m.set_params(*cp_params(p))
     m.set_test(p.test_idx, p.test_val)
     m.epoch("hogwild")
     L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 1))
@@ -477,10 +558,7 @@ def cp_hogwild(p, order, stream, epochs=3):
     L.check(m.lib, m.ctx, m.lib.s3_profile_read(m.ctx, L.S3_K_TENSOR_HOG, C.byref(kms),
                                                   C.byref(kn), C.byref(ke)))
     L.check(m.lib, m.ctx, m.lib.s3_profile(m.ctx, 0))
-    rows = sum(int(np.unique(p.train_idx[n]).shape[0]) for n in range(p.N))
-    rows += sum(int(np.unique(c.cols).shape[0]) for c in p.coupled)
-    ld = 4 * ((J + 3) // 4)
-    nbytes = p.nnz * (8 * p.N + 4) + sum(c.nnz * 20 for c in p.coupled) + rows * ld * 4 * 2
+    nbytes = cp_bytes(p)
     peaks, src = measured_peaks()
     k_ms = kms.value / epochs
     achieved = nbytes / (k_ms / 1000.0) / 1e9
@@ -609,6 +687,8 @@ def run_gradient(args, world, rank, local):
             dist.barrier()
 
     p = synth.make_problem(args.workload, seed=rank)
+    if args.rank:
+        p = synth.with_rank(p, (args.rank,) * p.N)
     stream = torch.cuda.Stream()
     model = S3CMTF.from_problem(p, order=synth.union_order(p, 2), stream=stream)
     model.set_params(*synth.init_params(p, 1))
@@ -645,8 +725,10 @@ def run_gradient(args, world, rank, local):
     fpe = flops_per_entry(p)
     achieved = fpe * k_entries / (k_ms / 1000.0) / 1e12 if k_ms > 0 else None
     fpk, fsrc = fp32_peak()
+    wl = args.workload + (f"@J{args.rank}" if args.rank else "")
     roofline = {"bound": "alu", "achieved": achieved, "peak": fpk, "unit": "TFLOP/s",
-                "frac": (achieved / fpk) if achieved else None, "traffic": None,
+                "frac": (achieved / fpk) if achieved else None,
+                "traffic": committed_traffic("k_tensor_contrib", wl),
                 "kernel": "k_tensor_contrib", "launches": k_n,
                 "kernel_ms_per_step": k_ms / args.steps, "flops_per_entry": fpe,
                 "peak_source": fsrc,
@@ -672,9 +754,12 @@ def run_gradient(args, world, rank, local):
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": job_rate(gb, args.steps, world, e2e_s) / 1e9, "unit": "GB/s",
-           "h2d_bytes_per_step": 4 * p.n_union, "d2h_bytes_per_step": d2h}
+           "h2d_bytes_per_step": 4 * p.n_union, "d2h_bytes_per_step": d2h,
+           "copies": "every step: the tensor and coupled values (FP32) from pinned host memory "
+                     "in, the whole gradient (core, every factor, every coupled factor) out; "
+                     "the coordinates stay resident"}
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
         import oracle
         S = max(1000, min(args.cpu_sample // 20, p.nnz))
         q = sub_problem(p, S, max(1, S // 2))
@@ -703,6 +788,49 @@ def run_gradient(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def _sig(x, n=4):
+    return None if x is None else float(f"{x:.{n}g}")
+
+
+def summary_of(extras):
+    """The side measurements' headline figures in a few hundred bytes (the full objects follow
+    in the line): per rank the BF16/FP32 epoch times, the BF16 speedup, both forms' largest
+    test-RMSE deviation from the oracle's Algorithm 1 curve (where one is stored) and the
+    gap between the two forms; the gradient pass in GB/s; the other epoch forms."""
+    out = {}
+    for key in ("forms_j10", "forms_j16", "forms_j20", "forms_j32"):
+        f = extras.get(key)
+        if not f:
+            continue
+        row = {"fp32_ms": _sig(f["fp32"]["ms_per_epoch"]), "bf16_ms": _sig(f["bf16"]["ms_per_epoch"]),
+               "bf16_speedup": _sig(f["bf16_speedup"], 3),
+               "bf16_tensor_frac": _sig(f["bf16"]["roofline"]["frac"], 3),
+               "fp32_ffma_frac": _sig(f["fp32"]["roofline"]["frac"], 3),
+               "rmse_gap_bf16_vs_fp32": _sig(f["rmse_max_rel_gap"], 2)}
+        v = f.get("vs_oracle_algorithm1")
+        if v:
+            row["max_dev_vs_alg1"] = {prec: _sig(max(abs(x) for x in v[prec]), 3) for prec in ("fp32", "bf16")}
+        out[key.replace("forms_", "")] = row
+    g = {}
+    if "gradient_pass" in extras:
+        g["cfg1"] = _sig(extras["gradient_pass"]["GB/s"])
+    if "gradient_pass_cfg3" in extras:
+        g["cfg3"] = _sig(extras["gradient_pass_cfg3"]["GB/s"])
+    if g:
+        out["gradient_pass_GBps"] = g
+    if "minibatch_epoch" in extras:
+        out["minibatch_ms"] = _sig(extras["minibatch_epoch"]["ms"])
+    if "cp_hogwild" in extras:
+        out["cp_ms"] = _sig(extras["cp_hogwild"]["ms_per_epoch"])
+    if "nonneg_hogwild" in extras:
+        out["nonneg_ms"] = _sig(extras["nonneg_hogwild"]["ms_per_epoch"])
+    sc = extras.get("scalability")
+    if sc:
+        out["scalability"] = {"r2_over_nnz": _sig(sc["linear_fit_r2"], 6),
+                              "time_ratio_across_I": _sig(sc["time_ratio_max_over_min_across_I"], 3)}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import ctypes as C
 
@@ -722,10 +850,13 @@ def run_ours(args, world, rank, local):
 
     # each rank fits its own replica problem (weak scaling)
     p = synth.make_problem(args.workload, seed=rank)
+    if args.rank:
+        p = synth.with_rank(p, (args.rank,) * p.N)
     order = synth.union_order(p, 2)
     stream = torch.cuda.Stream()
-    model = S3CMTF.from_problem(p, order=order, stream=stream)
-    model.set_params(*synth.init_params(p, 1))
+    variant = {"cp": dict(cp=1), "nonneg": dict(nonneg=1)}.get(args.variant, {})
+    model = S3CMTF.from_problem(p, order=order, stream=stream, **variant)
+    model.set_params(*(cp_params(p) if args.variant == "cp" else synth.init_params(p, 1)))
     model.set_test(p.test_idx, p.test_val)
     lib, ctx = model.lib, model.ctx
 
@@ -780,12 +911,23 @@ def run_ours(args, world, rank, local):
     else:
         peak, psrc = fp32_peak()
         bound = "alu"
-    traffic = committed_traffic(kname, args.workload)
+    wl = args.workload + (f"@J{args.rank}" if args.rank else "")
+    traffic = committed_traffic(kname, wl)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
                 "traffic": traffic, "kernel": kname, "launches": k_n,
                 "kernel_ms_per_step": k_ms / args.steps,
                 "flops_per_entry": flops_per_entry, "peak_source": psrc}
+    if args.variant == "cp" and args.mode == "hogwild":
+        # O(N J) work per entry: the bandwidth roof of its algorithmic bytes
+        peaks, src = measured_peaks()
+        nbytes = cp_bytes(p)
+        gbs = nbytes * k_n / (k_ms / 1000.0) / 1e9 if k_ms > 0 else None
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                    "traffic": committed_traffic("k_cp_hog", wl), "kernel": "k_cp_hog",
+                    "launches": k_n, "kernel_ms_per_step": k_ms / args.steps,
+                    "bytes_per_launch": nbytes, "peak_source": f"{src} hbm_gbs"}
 
     extras = {}
     if not args.no_extras:
@@ -848,18 +990,25 @@ def run_ours(args, world, rank, local):
     e2e_s = max_over_ranks(e2e_s, world)
     h2d = 4 * items + 4
     e2e = {"value": job_rate(items, args.steps, world, e2e_s), "unit": UNIT,
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 12,
+           "copies": "every step: the tensor and coupled values (FP32) from pinned host memory "
+                     "(s3_update_values) and the learning rate in, the test RMSE (FP64) and "
+                     "status out; the coordinates and the layout built from them stay resident "
+                     "(they are fixed for a fit)"}
 
     cpu = None
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
         cpu = cpu_baseline(p, min(args.cpu_sample, p.n_union), order)
+        # the oracle on every host core beside it (the minibatch rule, one batch, mode-1 parts)
+        cpu["all_cores"] = cpu_baseline_multicore(p, min(4 * args.cpu_sample, p.nnz))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+                "summary": summary_of(extras),
                 "config": dict(workload_desc(p, args.mode, args.precision),
-                               parallelism=f"replicas x{world}",
+                               parallelism=f"replicas x{world}", variant=args.variant,
                                hogwild_launch=hog_launch),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "updates_by_kind": split,

@@ -105,7 +105,7 @@ struct s3_ctx {
     size_t hog_smem = 0;
     int hog_lanes = 1;
     int mb_grid = 0;               // CTAs of the persistent minibatch epoch
-    unsigned* d_bar = nullptr;     // its grid-barrier counter and generation
+    unsigned* d_bar = nullptr;     // its grid-barrier arrival counter
     // measurement (s3_profile)
     bool prof = false;
     int64_t launches = 0;
@@ -525,7 +525,10 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
             }
         }
     }
-    const int64_t grad_chunk = hp->grad_chunk > 0 ? hp->grad_chunk : 1 << 20;
+    // 2^22 items per gradient chunk by default: on cfg1 (14M items) a pass took 4.09 ms in
+    // chunks of 2^20, 3.70 ms in chunks of 2^22 and 3.76 ms in one chunk (cfg3, 67M items:
+    // 58.9, 54.8 ms at 2^23, 55.2 ms in one), while the slots stay a few hundred MB
+    const int64_t grad_chunk = hp->grad_chunk > 0 ? hp->grad_chunk : 1 << 22;
     if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad, kShortSeg,
                                              kHugeSeg);
     if (!msg.empty()) return bail(S3_ERR_ARG, msg);
@@ -590,8 +593,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     CK(dalloc(ctx, &ctx->d_kerr, 1));
     CK(dalloc(ctx, &ctx->d_idx_bad, 1));
     CK(cudaMallocHost((void**)&ctx->h_idx_bad, sizeof(int)));
-    CK(dalloc(ctx, &ctx->d_bar, 2));
-    CK(cudaMemsetAsync(ctx->d_bar, 0, 2 * sizeof(unsigned), ctx->stream));
+    CK(dalloc(ctx, &ctx->d_bar, 1));
+    CK(cudaMemsetAsync(ctx->d_bar, 0, sizeof(unsigned), ctx->stream));
     // one CTA per SM by default: the epoch's grid-wide barriers cost more with every CTA
     // than a second co-resident CTA gains in latency hiding
     ctx->mb_grid = std::min<int>({minibatch_epoch_grid(N, ctx->JP, ctx->num_sms), ctx->num_sms,
@@ -619,8 +622,12 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         // as the plain group steps do, so that the plain form's stronger damping of hot rows
         // leaves it 2-3% above projected Algorithm 1, while this setting keeps it within 1%
         // (cfg1, rank 10: 0.82%).
-        const double gamma = hp->hog_staleness != 0.f ? (double)hp->hog_staleness
-                             : (hp->nonneg ? 2000.0 : 360.0) / jmax;
+        // Above rank 16 the plain form takes (360 / J) sqrt(16 / J), 7.95 at rank 32: there
+        // 360 / J = 11.25 left the first epoch 1.0% below Algorithm 1 (cfg1), 8 leaves it
+        // 0.4% (FP32) and 0.3% (BF16) below, 6 0.3% above and 4 1.3% above.
+        double gamma = (hp->nonneg ? 2000.0 : 360.0) / jmax;
+        if (!hp->nonneg && jmax > 16) gamma *= std::sqrt(16.0 / jmax);
+        if (hp->hog_staleness != 0.f) gamma = (double)hp->hog_staleness;
         auto row_scales = [&](DevGrouping& D, double inflight) -> int {
             for (int F = 0; F < nF; ++F) {
                 std::vector<float> d(occ[(size_t)F].size(), 1.f);
@@ -725,7 +732,6 @@ static int enqueue_minibatch(s3_ctx* ctx) {
     for (int F = 0; F < nF; ++F) L.contrib[F] = ctx->contrib[F];
     L.core_part = ctx->core_part;
     L.bar_count = ctx->d_bar;
-    L.bar_gen = ctx->d_bar + 1;
     L.err_flag = ctx->d_kerr;
     L.eta = ctx->d_eta;
     L.core_scale = ctx->hp.core_scale;

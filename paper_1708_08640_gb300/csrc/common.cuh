@@ -73,10 +73,14 @@ __device__ __forceinline__ void st4(float* p, float4 v) {
     *reinterpret_cast<float4*>(p) = v;
 }
 
-// Asynchronous 4-byte copy global -> shared (no register round trip); cp_async_wait_all
-// waits for every copy the thread issued.
+// Asynchronous 4- and 8-byte copies global -> shared (no register round trip; both addresses
+// aligned to the size); cp_async_wait_all waits for every copy the thread issued.
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;"
                  :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -128,22 +132,24 @@ struct Kahan {
 };
 
 // Compensated sums, component by component, of the rows src + e * ld (4 * C4 floats each,
-// 16-byte aligned) for e = e0, e0 + step, ... < cnt, added in that order; several rows'
-// loads are in flight at once.
+// 16-byte aligned) for e = e0, e0 + step, ... < cnt, added in that order; U rows' loads are
+// issued together (the last batch's with predicates), so a short sum costs one round trip.
 template <int C4>
 __device__ __forceinline__ void rows_sum(const float* src, int64_t ld, int e0, int step, int cnt,
                                          Kahan (&k)[4 * C4]) {
     constexpr int U = C4 <= 4 ? 4 : 2;
-    int e = e0;
-    for (; e + (U - 1) * step < cnt; e += U * step) {
+    for (int e = e0; e < cnt; e += U * step) {
         float4 v[U][C4];
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
             for (int q = 0; q < C4; ++q)
-                v[u][q] = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)(e + u * step) * ld + 4 * q));
+                v[u][q] = e + u * step < cnt
+                              ? __ldcg(reinterpret_cast<const float4*>(src + (int64_t)(e + u * step) * ld + 4 * q))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) {
+            if (e + u * step >= cnt) break;
 #pragma unroll
             for (int q = 0; q < C4; ++q) {
                 k[4 * q].add(v[u][q].x);
@@ -151,15 +157,6 @@ __device__ __forceinline__ void rows_sum(const float* src, int64_t ld, int e0, i
                 k[4 * q + 2].add(v[u][q].z);
                 k[4 * q + 3].add(v[u][q].w);
             }
-    }
-    for (; e < cnt; e += step) {
-#pragma unroll
-        for (int q = 0; q < C4; ++q) {
-            const float4 v = __ldcg(reinterpret_cast<const float4*>(src + (int64_t)e * ld + 4 * q));
-            k[4 * q].add(v.x);
-            k[4 * q + 1].add(v.y);
-            k[4 * q + 2].add(v.z);
-            k[4 * q + 3].add(v.w);
         }
     }
 }

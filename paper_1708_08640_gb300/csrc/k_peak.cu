@@ -87,7 +87,7 @@ extern "C" int s3_measure_fp32_peak(double* ffma_tflops, double* ffma2_tflops, d
         cudaStreamDestroy(st);
         return S3_ERR_OOM;
     }
-    const int iters = 1 << 11;   // about 0.2 s per launch at 80 TFLOP/s
+    const int iters = 1 << 11;   // 20 GFLOP a launch: about 0.26 ms at 80 TFLOP/s
     float ms1 = 0.f, ms2 = 0.f;
     cudaError_t e = time_kernel(k_peak_ffma, grid, iters, st, out, &ms1);
     if (e == cudaSuccess) e = time_kernel(k_peak_ffma2, grid, iters, st, out, &ms2);

@@ -60,8 +60,7 @@ cudaError_t launch_tensor_hog_bf16(int JP, const DParams& P, const DGroup& G, in
 struct MbLaunch {
     float* contrib[kMaxF];
     float* core_part;        // >= grid partials of JP^N floats
-    unsigned* bar_count;     // zero before the launch
-    unsigned* bar_gen;
+    unsigned* bar_count;     // cumulative grid-barrier arrivals: zero before the launch
     int* err_flag;
     const float* eta;
     float core_scale;

@@ -90,17 +90,17 @@ def _rows_subproblem(q, mode_rows, cpl_rows, cpl_cols):
 
 
 def test_full_size_gradient_on_sampled_rows(cuda_lib, rating_tensor):
-    """cfg1 at full size (9M train entries, 5M coupled entries, J = 10): the pass runs in 14
-    chunks of 2^20 items, as in the bench.  Sampled rows of every factor (rows of modest
-    count, and the hottest row of modes 2 and 3) against the oracle's gradient of the same
-    rows, computed from the entries that touch them."""
+    """cfg1 at full size (9M train entries, 5M coupled entries, J = 10): the pass runs in 4
+    chunks of 2^22 items (the default), as in the bench.  Sampled rows of every factor (rows
+    of modest count, and the hottest row of modes 2 and 3) against the oracle's gradient of
+    the same rows, computed from the entries that touch them."""
     p = rating_tensor
     q = fp32_problem(p)
     params = fp32_params(synth.init_params(p, 1))
     from paper_1708_08640_gb300.model import S3CMTF
     gpu = S3CMTF.from_problem(q, order=synth.union_order(p, 2))
     gpu.set_params(*params)
-    assert -(-p.n_union // (1 << 20)) == 14
+    assert -(-p.n_union // (1 << 22)) == 4
     dG, dU, dV = gpu.gradient()
     rng = np.random.default_rng(11)
     mode_rows = {}

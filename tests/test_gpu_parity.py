@@ -97,6 +97,27 @@ def test_minibatch_epochs_track_oracle(cuda_lib, problems, row_rule):
         assert rel(as_np(U[n]), orc.U[n]) <= 1e-4
 
 
+@pytest.mark.parametrize("row_rule", ["sum", "mean"])
+def test_minibatch_epochs_track_oracle_4way(cuda_lib, problems, row_rule):
+    """The deterministic epoch on the 4-way cfg3_tiny data (two coupled matrices, batches of
+    1024 items, both row rules): test RMSE within 1e-4 relative of the FP64 oracle's after
+    each of 3 epochs, parameters within 1e-4."""
+    p = problems["cfg3_tiny"]
+    gpu, orc, q, order = make_pair(p, batch=1024, row_rule=row_rule)
+    for t in range(3):
+        gpu.epoch("minibatch")
+        orc.epoch_minibatch(t, order)
+        a, b = gpu.rmse(q.test_idx, q.test_val), orc.rmse(q.test_idx, q.test_val)
+        assert np.isfinite(b)
+        assert abs(a - b) / b <= 1e-4, (t, a, b)
+    G, U, V = gpu.get_params()
+    assert rel(as_np(G), orc.G) <= 1e-4
+    for n in range(p.N):
+        assert rel(as_np(U[n]), orc.U[n]) <= 1e-4
+    for m in range(len(p.coupled)):
+        assert rel(as_np(V[m]), orc.V[m]) <= 1e-4
+
+
 def test_minibatch_curve_cfg1_tiny(cuda_lib, problems):
     p = problems["cfg1_tiny"]
     gpu, orc, q, order = make_pair(p)
