@@ -16,6 +16,7 @@ both the CUDA path and the oracle as inputs.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -68,6 +69,33 @@ class Problem:
 
 # ----------------------------------------------------------------------------- samplers
 
+def _in_slices(n, fn, chunk=1 << 22):
+    """fn(slice) over [0, n) in slices of `chunk`, on a pool of host threads for large n
+    (numpy releases the interpreter lock in these loops). Every slice is computed as it
+    would be alone, so the results do not depend on the thread count."""
+    slices = [slice(s, min(n, s + chunk)) for s in range(0, n, chunk)]
+    workers = min(len(slices), os.cpu_count() or 1)
+    if workers <= 1:
+        for sl in slices:
+            fn(sl)
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(workers) as pool:
+        list(pool.map(fn, slices))
+
+
+def _zipf_ranks(cdf, u):
+    """Ranks of the uniform draws u under the CDF cdf (searchsorted, clipped), by slices."""
+    rank = np.empty(u.shape[0], dtype=np.int64)
+
+    def one(sl):
+        r = np.searchsorted(cdf, u[sl], side="right")
+        np.minimum(r, cdf.shape[0] - 1, out=r)
+        rank[sl] = r
+    _in_slices(u.shape[0], one)
+    return rank
+
+
 def zipf_sample(rng, n, support, s):
     """Draw ``n`` ids from a finite Zipf law p_k ~ k^-s over ranks 1..support.
 
@@ -77,22 +105,28 @@ def zipf_sample(rng, n, support, s):
     w = np.arange(1, support + 1, dtype=np.float64) ** (-float(s))
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
-    rank = np.searchsorted(cdf, rng.random(n), side="right")
-    np.minimum(rank, support - 1, out=rank)
+    rank = _zipf_ranks(cdf, rng.random(n))
     perm = rng.permutation(support)
     return perm[rank].astype(np.int64)
 
 
 def _merge_unique(keys, new):
     """Sorted distinct values of keys (sorted, distinct) together with new: the same result
-    as numpy.unique(numpy.concatenate([keys, new])), by a stable sort and a neighbour test."""
-    s = np.sort(np.concatenate([keys, new]), kind="stable")
-    if s.shape[0] == 0:
-        return s
-    keep = np.empty(s.shape[0], dtype=bool)
-    keep[0] = True
-    np.not_equal(s[1:], s[:-1], out=keep[1:])
-    return s[keep]
+    as numpy.unique(numpy.concatenate([keys, new])), by sorting only the new values and
+    inserting those not present at their positions."""
+    new = np.sort(new)
+    if new.shape[0] > 1:
+        first = np.empty(new.shape[0], dtype=bool)
+        first[0] = True
+        np.not_equal(new[1:], new[:-1], out=first[1:])
+        new = new[first]
+    if keys.shape[0] == 0:
+        return new
+    pos = np.searchsorted(keys, new)
+    present = keys[np.minimum(pos, keys.shape[0] - 1)] == new
+    present &= pos < keys.shape[0]
+    keep = ~present
+    return np.insert(keys, pos[keep], new[keep])
 
 
 def _draw_coords(rng, n, dims, laws, perms):
@@ -105,9 +139,13 @@ def _draw_coords(rng, n, dims, laws, perms):
             w = np.arange(1, d + 1, dtype=np.float64) ** (-s)
             cdf = np.cumsum(w)
             cdf /= cdf[-1]
-            rank = np.searchsorted(cdf, rng.random(n), side="right")
-            np.minimum(rank, d - 1, out=rank)
-            cols.append(perm[rank].astype(np.int64))
+            rank = _zipf_ranks(cdf, rng.random(n))
+            ids = np.empty(n, dtype=np.int64)
+
+            def gather(sl, ids=ids, rank=rank, perm=perm):
+                ids[sl] = perm[rank[sl]]
+            _in_slices(n, gather)
+            cols.append(ids)
     return cols
 
 
@@ -166,12 +204,13 @@ def _planted_values(G, U, idx, chunk=1 << 17):
     # contract the last mode against every row of U[N-1] once
     T = np.tensordot(U[N - 1], G, axes=([1], [N - 1]))      # (I_N, J_1..J_{N-1})
     out = np.empty(idx.shape[1], dtype=np.float64)
-    for s in range(0, idx.shape[1], chunk):
-        e = slice(s, s + chunk)
+
+    def one(e):
         t = T[idx[N - 1, e]]
         for n in range(N - 2, -1, -1):
             t = np.einsum("c...j,cj->c...", t, U[n][idx[n, e]])
         out[e] = t
+    _in_slices(idx.shape[1], one, chunk)
     return out
 
 

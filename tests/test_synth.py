@@ -67,3 +67,31 @@ def test_fourway_and_scalability_presets():
     assert p.coupled[0].nnz == 300
     with pytest.raises(ValueError):
         synth.unique_coords(np.random.default_rng(0), 10, (2, 2), ("uniform", "uniform"))
+
+
+def test_incremental_unique_merge_equals_numpy_unique():
+    """The generators' redraw loop keeps the sorted distinct coordinates by inserting each
+    redraw's new keys; the result is numpy.unique of everything drawn so far."""
+    rng = np.random.default_rng(5)
+    keys = np.empty(0, dtype=np.int64)
+    seen = np.empty(0, dtype=np.int64)
+    for _ in range(50):
+        new = rng.integers(0, 400, size=int(rng.integers(0, 60)))
+        keys = synth._merge_unique(keys, new)
+        seen = np.concatenate([seen, new])
+        assert np.array_equal(keys, np.unique(seen))
+
+
+def test_planted_values_do_not_depend_on_slicing():
+    """The planted model is evaluated in slices on host threads; every slice is computed
+    alone, so any slice size gives the same values bit for bit."""
+    rng = np.random.default_rng(6)
+    dims, J = (40, 30, 20), (3, 4, 5)
+    G = rng.standard_normal(J)
+    U = [rng.random((d, j)) for d, j in zip(dims, J)]
+    idx = np.stack([rng.integers(0, d, size=5000) for d in dims])
+    a = synth._planted_values(G, U, idx, chunk=1 << 17)
+    b = synth._planted_values(G, U, idx, chunk=97)
+    assert np.array_equal(a, b)
+    ref = np.einsum("abc,ea,eb,ec->e", G, U[0][idx[0]], U[1][idx[1]], U[2][idx[2]])
+    assert np.allclose(a, ref, rtol=1e-12, atol=1e-12)
