@@ -91,6 +91,11 @@ def parse():
     ap.add_argument("--rank", type=int, default=0,
                     help="run the workload at rank J in every mode instead of its own "
                          "(rating workloads, e.g. --workload cfg1_small --rank 32)")
+    ap.add_argument("--forms", action="store_true",
+                    help="also run both precision forms of the HOGWILD epoch on the step's data "
+                         "at its own rank (--steps epochs each) and report the comparison "
+                         "(with --no-extras: the BF16 vs FP32 comparison of a large workload "
+                         "from one generation of its data)")
     ap.add_argument("--variant", choices=["plain", "cp", "nonneg"], default="plain",
                     help="the step's method: plain S3CMTF-TUCKER, S3CMTF-CP (hyper-diagonal "
                          "core) or the non-negative form (projected SGD)")
@@ -375,13 +380,16 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- forms
-def precision_forms(p, order, stream, args, J=16, epochs=4):
+def precision_forms(p, order, stream, args, J=16, epochs=4, model=None):
     """The FP32 and BF16 forms of the HOGWILD epoch on the same data at rank J (the cfg2
     workloads, J = 16 and 32, and the cfg1 data at J = 10 and 20): epoch time, nnz-updates/s, test RMSE after every epoch (the
     "matched RMSE" check: the largest relative gap between the two forms' curves), and the
     tensor-pass kernel's roofline (FP32 FFMA roof for the FP32 form, BF16 tensor roof for
     the BF16 form).  Epochs are timed one by one with CUDA events; the RMSE reads between
-    them are outside the timed regions."""
+    them are outside the timed regions.  With `model` (a context of p at rank J, with its
+    test set) both forms run on it, each from the same start (parameters and epoch counter
+    reset): one copy of the layout on the device instead of two, for workloads whose layout
+    fills much of HBM."""
     import ctypes as C
 
     import torch
@@ -394,9 +402,13 @@ def precision_forms(p, order, stream, args, J=16, epochs=4):
     out = {}
     flops_entry = 6.0 * J ** 3
     for prec in ("fp32", "bf16"):
-        m = S3CMTF.from_problem(q, order=order, stream=stream)
+        if model is not None:
+            m = model
+            m.epoch_count = 0
+        else:
+            m = S3CMTF.from_problem(q, order=order, stream=stream)
+            m.set_test(q.test_idx, q.test_val)
         m.set_params(*init)
-        m.set_test(q.test_idx, q.test_val)
         curve = []
         m.epoch("hogwild", prec)          # warm-up epoch (its RMSE is the curve's first point)
         curve.append(m.rmse())
@@ -428,7 +440,8 @@ def precision_forms(p, order, stream, args, J=16, epochs=4):
         out[prec] = {"ms_per_epoch": ms, "nnz_updates_per_s": q.n_union / (ms / 1000.0),
                      "test_rmse": curve, "epochs": 1 + epochs, "roofline": roof,
                      "launch": m.hog_config(prec)}
-        m.close()
+        if model is None:
+            m.close()
     # each form's test RMSE per epoch against the FP64 oracle's Algorithm 1 curve on the same
     # data, rank, start and order, where one is stored (tests/golden, written by the oracle)
     ref = stored_curve(q, "sequential")
@@ -930,6 +943,9 @@ def run_ours(args, world, rank, local):
                     "bytes_per_launch": nbytes, "peak_source": f"{src} hbm_gbs"}
 
     extras = {}
+    if args.forms and p.N == 3 and len(set(p.J)) == 1:
+        extras[f"forms_j{p.J[0]}"] = precision_forms(p, order, stream, args, J=p.J[0],
+                                                     epochs=args.steps, model=model)
     if not args.no_extras:
         # gradient pass (differentiation form): bytes moved per pass / time
         model.gradient()

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.h"
@@ -252,6 +253,29 @@ static int upload_grouping(s3_ctx* ctx, const HostGrouping& H, DevGrouping& D) {
     return S3_OK;
 }
 
+// frees a host grouping's per-item arrays once they are on the device (its per-group offsets
+// and sizes stay: the launches are sized from them)
+static void release_items(HostGrouping& H) {
+    auto drop = [](auto& v) { std::decay_t<decltype(v)>().swap(v); };
+    for (auto& v : H.tidx) drop(v);
+    for (auto& v : H.tpos) drop(v);
+    drop(H.tval);
+    drop(H.t_src);
+    for (int m = 0; m < 8; ++m) {
+        drop(H.cr[m]);
+        drop(H.cc[m]);
+        drop(H.cval[m]);
+        drop(H.cpos_u[m]);
+        drop(H.cpos_v[m]);
+        drop(H.c_src[m]);
+    }
+    for (int F = 0; F < 12; ++F) {
+        drop(H.seg_row[F]);
+        drop(H.seg_start[F]);
+        drop(H.seg_cnt[F]);
+    }
+}
+
 static void fill_params(s3_ctx* ctx) {
     DParams& P = ctx->P;
     P.N = ctx->N;
@@ -433,6 +457,15 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     }
     HostGrouping hmb, hhog, hgrad, hhog_bf;
     const int nF = N + n_coupled;
+    // each grouping goes to the device as soon as it is built, and its per-item host arrays
+    // are freed then, so that the host holds one grouping at a time (about 70 bytes per item)
+    *out = ctx;
+    auto place = [&](HostGrouping& H, DevGrouping& D) -> int {
+        const int rc = upload_grouping(ctx, H, D);
+        if (rc == S3_OK) release_items(H);
+        return rc;
+    };
+    int rc_up = S3_OK;
     // FP32 HOGWILD tiles hold at most T / 2 entries for 3-way tensors (T compute threads,
     // two lanes per entry; tiles of up to T / 4 entries take four), T for 4-way (one lane),
     // T = hog_compute_threads.  Default for 3-way tensors: the largest tile (192 entries up
@@ -458,7 +491,9 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     const int64_t budget = hog_inflight_budget(jmax) * (hp->nonneg ? 3 : 4) / 4;
     ctx->bf_jp = ctx->JP <= 16 ? 16 : (ctx->JP == 20 ? 20 : 32);
     std::string msg = build_grouping(in, hord.data(), ctx->n_union, RULE_UNION, hp->batch, POS_SLOT, hmb, kShortSeg);
+    if (msg.empty() && (rc_up = place(hmb, ctx->mb)) != S3_OK) return rc_up;
     if (msg.empty()) msg = build_grouping(in, hord.data(), ctx->n_union, RULE_TENSOR, tile, POS_SLOT, hhog);
+    if (msg.empty() && (rc_up = place(hhog, ctx->hog)) != S3_OK) return rc_up;
     // HOGWILD concurrency of the FP32 form: CTAs resident at once, each on a tile of `tile`
     // entries
     if (msg.empty()) {
@@ -524,6 +559,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
                 break;
             }
         }
+        if (msg.empty() && (rc_up = place(hhog_bf, ctx->hog_bf)) != S3_OK) return rc_up;
     }
     // 2^22 items per gradient chunk by default: on cfg1 (14M items) a pass took 4.09 ms in
     // chunks of 2^20, 3.70 ms in chunks of 2^22 and 3.76 ms in one chunk (cfg3, 67M items:
@@ -531,8 +567,8 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     const int64_t grad_chunk = hp->grad_chunk > 0 ? hp->grad_chunk : 1 << 22;
     if (msg.empty()) msg = build_grouping(in, nullptr, ctx->n_union, RULE_UNION, grad_chunk, POS_SLOT, hgrad, kShortSeg,
                                              kHugeSeg);
+    if (msg.empty() && (rc_up = place(hgrad, ctx->grad)) != S3_OK) return rc_up;
     if (!msg.empty()) return bail(S3_ERR_ARG, msg);
-    *out = ctx;
     // ---- device buffers
     for (int n = 0; n < N; ++n) {
         CK(dalloc(ctx, &ctx->P.U[n], (size_t)ctx->I[n] * ctx->JPR));
@@ -566,10 +602,6 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         for (int64_t b = 0; b < ctx->ynnz[m]; ++b) occ[(size_t)ctx->cmode[m]][(size_t)hyr[m][(size_t)b]]++;
     fill_params(ctx);
     int rc;
-    if ((rc = upload_grouping(ctx, hmb, ctx->mb)) != S3_OK) return rc;
-    if ((rc = upload_grouping(ctx, hhog, ctx->hog)) != S3_OK) return rc;
-    if ((rc = upload_grouping(ctx, hgrad, ctx->grad)) != S3_OK) return rc;
-    if (bf16_ok && (rc = upload_grouping(ctx, hhog_bf, ctx->hog_bf)) != S3_OK) return rc;
     // scratch: contribution slots (minibatch and gradient groups), core partials
     for (int F = 0; F < nF; ++F) {
         const int64_t ev = std::max(ctx->mb.max_ev[F], ctx->grad.max_ev[F]);
