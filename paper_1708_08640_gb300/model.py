@@ -8,6 +8,8 @@ from __future__ import annotations
 
 import ctypes as C
 
+import os
+
 import numpy as np
 import torch
 
@@ -46,6 +48,8 @@ class S3CMTF:
                  device=None,
                  stream=None):
         self.lib = L.load()
+        self.lr0, self.mu = float(lr0), float(mu)
+        self._has_test = False
         self.device = torch.device(device if device is not None else "cuda")
         if self.device.type != "cuda":
             raise ValueError("S3CMTF runs on a CUDA device")
@@ -134,6 +138,43 @@ class S3CMTF:
     def epoch(self, mode="minibatch", precision="fp32"):
         self._check(self.lib.s3_epoch(self.ctx, _MODES[mode], _PREC[precision]))
 
+    def fit(self, epochs, mode="hogwild", precision="fp32", log=None):
+        """Runs `epochs` epochs and returns one record per epoch: its number t (from 0, the
+        context's counter), the learning rate eta_t = lr0 / (1 + mu t) it used (Section 3.4),
+        the loss f of Eq. (7) and the RMSE over the training entries after it, the test RMSE
+        (None without a test set), the epoch's device time in ms (CUDA events on the
+        context's stream; the loss and RMSE reads are outside it) and the nnz-updates/s that
+        time gives (tensor plus coupled entries).  With `log` (a path, opened for appending,
+        or a writable text file) every record is also written as one JSON line when its
+        epoch ends."""
+        import json
+        out = []
+        fh = open(log, "a") if isinstance(log, (str, os.PathLike)) else log
+        try:
+            n_items = self.info()["n_union"]
+            for _ in range(int(epochs)):
+                t = self.epoch_count
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(self.stream)
+                self.epoch(mode, precision)
+                e1.record(self.stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                f, train_rmse = self.loss()
+                rec = {"epoch": t, "eta": self.lr0 / (1.0 + self.mu * t), "mode": mode,
+                       "precision": precision, "loss": f, "train_rmse": train_rmse,
+                       "test_rmse": self.rmse() if self._has_test else None,
+                       "epoch_ms": ms, "nnz_updates_per_s": n_items / (ms / 1000.0)}
+                out.append(rec)
+                if fh is not None:
+                    fh.write(json.dumps(rec) + "\n")
+                    fh.flush()
+        finally:
+            if fh is not None and fh is not log:
+                fh.close()
+        return out
+
     def loss(self):
         f, r = C.c_double(), C.c_double()
         self._check(self.lib.s3_loss(self.ctx, C.byref(f), C.byref(r)))
@@ -146,6 +187,7 @@ class S3CMTF:
         t = L.s3_coo_tensor(self.N, self._dims_arr, int(val.shape[0]),
                             L.ptr_array([a.ctypes.data for a in rows]), val.ctypes.data)
         self._check(self.lib.s3_set_test(self.ctx, C.byref(t), 0))
+        self._has_test = True
 
     def rmse(self, idx=None, val=None):
         out = C.c_double()
