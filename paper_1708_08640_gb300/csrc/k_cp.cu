@@ -53,7 +53,9 @@ __global__ void __launch_bounds__(kCpThreads) k_cp_hog(DParams P, DGroup Gr, int
         const int64_t e0 = s_lo[0];
         const int nb = (int)(s_hi[0] - e0);
         hog_tables_async(P, Gr, s_lo, s_hi, smem, H, tid, kCpThreads);
-        if (tid < JP) s_lam[tid] = __ldcg(P.G + cp_diag(N, JP, P.ldg, tid));
+        // the diagonal is read by the warp after the one whose threads add to it, so that no
+        // load waits for the same thread's reduction of the previous tile
+        if (tid >= 32 && tid < 32 + JP) s_lam[tid - 32] = __ldcg(P.G + cp_diag(N, JP, P.ldg, tid - 32));
         __syncthreads();
         float gd[JP];   // this entry's e * prod_n a_n, the diagonal's gradient (negated)
 #pragma unroll

@@ -111,9 +111,12 @@ k_tensor_hog(DParams P, DGroup Gr, int64_t n_tiles,
         if (t >= n_tiles) break;
         {
             // the current core (coherent: other CTAs add to it), once the tile's row gathers
-            // are in flight
+            // are in flight.  Thread t reloads the quads that thread t + 32 reduced in the
+            // previous tile's core step, not its own: a load after the same thread's reduction
+            // to the same address waits until the reduction is done at L2, which put the
+            // whole reduction round trip in front of every tile.
             auto reload_core = [&]() {
-                for (int l = tid * 4; l < GF; l += kT * 4) st4(sG + l, ld4_cg(P.G + l));
+                for (int l = ((tid + 32) % kT) * 4; l < GF; l += kT * 4) st4(sG + l, ld4_cg(P.G + l));
                 compute_barrier<kT>();
             };
             const int nb = mb[kMetaNb];
