@@ -862,13 +862,18 @@ def run_ours(args, world, rank, local):
             dist.barrier()
 
     # each rank fits its own replica problem (weak scaling)
+    t_gen = time.perf_counter()
     p = synth.make_problem(args.workload, seed=rank)
     if args.rank:
         p = synth.with_rank(p, (args.rank,) * p.N)
     order = synth.union_order(p, 2)
+    t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream()
     variant = {"cp": dict(cp=1), "nonneg": dict(nonneg=1)}.get(args.variant, {})
+    t_init = time.perf_counter()
     model = S3CMTF.from_problem(p, order=order, stream=stream, **variant)
+    torch.cuda.synchronize()
+    t_init = time.perf_counter() - t_init
     model.set_params(*(cp_params(p) if args.variant == "cp" else synth.init_params(p, 1)))
     model.set_test(p.test_idx, p.test_val)
     lib, ctx = model.lib, model.ctx
@@ -1025,6 +1030,9 @@ def run_ours(args, world, rank, local):
                 "summary": summary_of(extras),
                 "config": dict(workload_desc(p, args.mode, args.precision),
                                parallelism=f"replicas x{world}", variant=args.variant,
+                               setup_s={"generate": round(t_gen, 2), "init": round(t_init, 2),
+                                        "init_what": "s3_init: inputs validated, layouts built "
+                                                     "on the host and uploaded"},
                                hogwild_launch=hog_launch),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "updates_by_kind": split,
