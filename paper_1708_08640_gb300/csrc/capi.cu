@@ -84,6 +84,8 @@ struct s3_ctx {
     float* contrib[kMaxF] = {};
     float* core_part = nullptr;
     int64_t core_part_n = 0;       // partial slots
+    float* seg_parts = nullptr;    // gradient pass: sums of the huge segments' pieces
+    int* seg_done = nullptr;       // and their completion counts (zero between launches)
     float* red_parts = nullptr;
     int64_t red_parts_n = 0;       // float pairs
     double* d_red = nullptr;
@@ -616,6 +618,19 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         ctx->core_part_n = parts;
         CK(dalloc(ctx, &ctx->core_part, (size_t)(parts * pd)));
     }
+    {
+        // the gradient pass's huge segments are summed in kHugeParts pieces each (k_segments):
+        // room for the most huge segments of any gradient chunk
+        int64_t hmax = 0;
+        for (int64_t g = 0; g < ctx->grad.ngroups; ++g) {
+            int64_t h = 0;
+            for (int F = 0; F < nF; ++F) h += ctx->grad.seg_nhuge[F][(size_t)g];
+            hmax = std::max(hmax, h);
+        }
+        CK(dalloc(ctx, &ctx->seg_parts, (size_t)std::max<int64_t>(hmax, 1) * kHugeParts * ctx->JPR));
+        CK(dalloc(ctx, &ctx->seg_done, (size_t)std::max<int64_t>(hmax, 1)));
+        CK(cudaMemsetAsync(ctx->seg_done, 0, (size_t)std::max<int64_t>(hmax, 1) * sizeof(int), ctx->stream));
+    }
     CK(dalloc(ctx, &ctx->d_red, 64));
     CK(cudaMallocHost((void**)&ctx->h_red, 64 * sizeof(double)));
     CK(dalloc(ctx, &ctx->d_eta, 1));
@@ -1093,6 +1108,8 @@ extern "C" int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const*
         SegmentLaunch S{};
         S.nF = nF;
         S.g = g;
+        S.part_sums = ctx->seg_parts;
+        S.part_done = ctx->seg_done;
         for (int F = 0; F < nF; ++F) {
             S.contrib[F] = ctx->contrib[F];
             S.out[F] = outs[F];

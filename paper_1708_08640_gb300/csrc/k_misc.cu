@@ -165,20 +165,26 @@ __global__ void __launch_bounds__(256) k_segments(DParams P, DGroup Gr, SegmentL
     const int64_t gthread = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     __shared__ float red[8][4 * C4];
-    // pass 0: a CTA per huge segment
-    for (int64_t w = blockIdx.x; w < S.huge_begin[S.nF]; w += gridDim.x) {
+    // pass 0: kHugeParts CTAs per huge segment, each on a contiguous piece of its events (a
+    // fixed cut, whatever the grid); the CTA that completes a segment adds the pieces' sums in
+    // piece order (deterministic), so one segment's events stream on many SMs at once
+    __shared__ int s_last;
+    for (int64_t w = blockIdx.x; w < S.huge_begin[S.nF] * kHugeParts; w += gridDim.x) {
+        const int64_t h = w / kHugeParts;
+        const int part = (int)(w % kHugeParts);
         int F = 0;
-        while (F + 1 < S.nF && w >= S.huge_begin[F + 1]) ++F;
-        const int64_t sg = Gr.seg_off[F][S.g] + (w - S.huge_begin[F]);
+        while (F + 1 < S.nF && h >= S.huge_begin[F + 1]) ++F;
+        const int64_t sg = Gr.seg_off[F][S.g] + (h - S.huge_begin[F]);
         const int32_t cnt = __ldg(Gr.seg_cnt[F] + sg);
         const int32_t row = __ldg(Gr.seg_row[F] + sg);
-        const float* src = S.contrib[F] + (int64_t)__ldg(Gr.seg_start[F] + sg) * ld;
+        const int64_t e0 = (int64_t)cnt * part / kHugeParts, e1 = (int64_t)cnt * (part + 1) / kHugeParts;
+        const float* src = S.contrib[F] + ((int64_t)__ldg(Gr.seg_start[F] + sg) + e0) * ld;
         float sum[4 * C4];
         {
             Kahan k[4 * C4];
 #pragma unroll
             for (int j = 0; j < 4 * C4; ++j) k[j].init();
-            rows_sum<C4>(src, ld, threadIdx.x, blockDim.x, cnt, k);
+            rows_sum<C4>(src, ld, threadIdx.x, blockDim.x, (int)(e1 - e0), k);
 #pragma unroll
             for (int j = 0; j < 4 * C4; ++j) sum[j] = k[j].value();
         }
@@ -190,11 +196,31 @@ __global__ void __launch_bounds__(256) k_segments(DParams P, DGroup Gr, SegmentL
 #pragma unroll
             for (int j = 0; j < 4 * C4; ++j) red[warp][j] = sum[j];
         __syncthreads();
+        float* mine = S.part_sums + (h * kHugeParts + part) * ld;
         if (threadIdx.x < ld) {
             const int j = threadIdx.x;
             Kahan k;
             k.init();
             for (int i = 0; i < (int)(blockDim.x >> 5); ++i) k.add(red[i][j]);
+            mine[j] = k.value();
+            __threadfence();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int done = atomicAdd(S.part_done + h, 1);
+            s_last = done == kHugeParts - 1;
+            if (s_last) {
+                S.part_done[h] = 0;   // ready for the next launch
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x < ld) {
+            const int j = threadIdx.x;
+            Kahan k;
+            k.init();
+            const float* all = S.part_sums + h * kHugeParts * ld;
+            for (int q = 0; q < kHugeParts; ++q) k.add(__ldcg(all + q * ld + j));
             float one[4 * C4];
 #pragma unroll
             for (int i = 0; i < 4 * C4; ++i) one[i] = 0.f;
@@ -253,8 +279,9 @@ __global__ void __launch_bounds__(256) k_segments(DParams P, DGroup Gr, SegmentL
 
 cudaError_t launch_segments(const DParams& P, const DGroup& G, const SegmentLaunch& S,
                             const float* eta, int row_mean, int mode, cudaStream_t s) {
+    if (S.huge_begin[S.nF] > 0 && (!S.part_sums || !S.part_done)) return cudaErrorInvalidValue;
     const int64_t work = std::max({S.short_begin[S.nF], 32 * S.long_begin[S.nF],
-                                   256 * S.huge_begin[S.nF]});
+                                   256 * kHugeParts * S.huge_begin[S.nF]});
     if (work <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)std::min<int64_t>((work + 255) / 256, 4096);
     S3_DISPATCH_C4(P.ld / 4, (k_segments<C4><<<grid, 256, 0, s>>>(P, G, S, eta, row_mean, mode)));

@@ -130,7 +130,13 @@ struct SegmentLaunch {
     int64_t huge_begin[kMaxF + 1];
     int64_t long_begin[kMaxF + 1];    // long, not huge
     int64_t short_begin[kMaxF + 1];
+    // a huge segment is summed in kHugeParts contiguous pieces by as many CTAs; each piece's
+    // sums go to part_sums[huge index][piece][4 * C4] and the CTA that completes the segment
+    // (part_done[huge index], zero between launches) adds them in piece order
+    float* part_sums;
+    int* part_done;
 };
+constexpr int kHugeParts = 16;
 cudaError_t launch_segments(const DParams& P, const DGroup& G, const SegmentLaunch& S,
                             const float* eta, int row_mean, int mode, cudaStream_t s);
 
