@@ -163,8 +163,15 @@ __device__ __forceinline__ float partials4(const float* __restrict__ sG, const f
                                            float (&p2)[JP], float (&p3)[JP], float (&p4)[JP]) {
     constexpr int JPR = round4(JP);
     constexpr int U1 = JP <= 4 ? JP : 1;
+    // the inner products over j4 and the p4 updates in pairs of j4 (packed FMAs); the j3
+    // terms of p1 and p2 share one sum s3 = sum_j3 t a3[j3] per (j1, j2)
+    constexpr int J2 = JP / 2;
+    static_assert(JP % 2 == 0, "packed form for even ranks");
+    float2 p4v[J2];
 #pragma unroll
-    for (int j = 0; j < JP; ++j) { p1[j] = 0.f; p2[j] = 0.f; p3[j] = 0.f; p4[j] = 0.f; }
+    for (int j = 0; j < J2; ++j) p4v[j] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < JP; ++j) { p1[j] = 0.f; p2[j] = 0.f; p3[j] = 0.f; }
 #pragma unroll U1
     for (int j1 = 0; j1 < JP; ++j1) {
         const float a1j = a1[j1];
@@ -172,23 +179,33 @@ __device__ __forceinline__ float partials4(const float* __restrict__ sG, const f
 #pragma unroll
         for (int j2 = 0; j2 < JP; ++j2) {
             const float w12 = a1j * a2[j2];
+            float s3 = 0.f;   // sum_j3 t(j3) a3[j3]
 #pragma unroll
             for (int j3 = 0; j3 < JP; ++j3) {
                 float g[JP];
                 load_grow<JP>(sG + ((j1 * JP + j2) * JP + j3) * JPR, g);
                 const float w = w12 * a3[j3];
-                float t = 0.f;
+                const float2 ww = make_float2(w, w);
+                float2 tt = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int j4 = 0; j4 < JP; ++j4) {
-                    t = fmaf(g[j4], a4[j4], t);
-                    p4[j4] = fmaf(g[j4], w, p4[j4]);
+                for (int j = 0; j < J2; ++j) {
+                    const float2 gg = make_float2(g[2 * j], g[2 * j + 1]);
+                    tt = __ffma2_rn(gg, make_float2(a4[2 * j], a4[2 * j + 1]), tt);
+                    p4v[j] = __ffma2_rn(gg, ww, p4v[j]);
                 }
+                const float t = tt.x + tt.y;
                 p3[j3] = fmaf(t, w12, p3[j3]);
-                p1j = fmaf(t, a2[j2] * a3[j3], p1j);
-                p2[j2] = fmaf(t, a1j * a3[j3], p2[j2]);
+                s3 = fmaf(t, a3[j3], s3);
             }
+            p1j = fmaf(s3, a2[j2], p1j);
+            p2[j2] = fmaf(s3, a1j, p2[j2]);
         }
         p1[j1] = p1j;
+    }
+#pragma unroll
+    for (int j = 0; j < J2; ++j) {
+        p4[2 * j] = p4v[j].x;
+        p4[2 * j + 1] = p4v[j].y;
     }
     float xt = 0.f;
 #pragma unroll
