@@ -139,8 +139,8 @@ typedef struct {
     int hog_core_sync;  /* BF16 HOGWILD: tiles over which a CTA accumulates its tiles' core steps
                            (in tensor memory) before adding them to G, lock-free, and re-reading
                            the core; between two such points the CTA computes with its own BF16
-                           copy of the core.  0 = default: 1 at computed rank 16, 2 at 20, 4 at
-                           32.  1 = the per-tile core step of the FP32 form. */
+                           copy of the core.  0 = default, by the padded rank: 1 up to 10, 2
+                           up to 20, 4 above.  1 = the per-tile core step of the FP32 form. */
     int wait_limit_us;  /* how long a bounded wait inside an epoch kernel (the minibatch epoch's
                            grid barrier, the BF16 kernel's tensor-core hand-offs) may last before
                            the kernel gives up, records where, and the epoch returns S3_ERR_CUDA

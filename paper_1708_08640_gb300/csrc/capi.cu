@@ -534,7 +534,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
     // and coupled entries would not fit in shared memory.
     int64_t bf_tile = tensor_hog_bf16_tile();
     if (msg.empty() && bf16_ok) {
-        ctx->hog_bf_sync = hp->hog_core_sync > 0 ? hp->hog_core_sync : tensor_hog_bf16_core_sync(ctx->bf_jp);
+        ctx->hog_bf_sync = hp->hog_core_sync > 0 ? hp->hog_core_sync : tensor_hog_bf16_core_sync(ctx->JP);
         const int64_t full = tensor_hog_bf16_tile();
         const int64_t inflight = ctx->hog_grid * ctx->hog_tile;
         int64_t want_ctas = 0, t0 = full;
