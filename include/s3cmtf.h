@@ -267,8 +267,10 @@ int s3_set_epoch(s3_ctx* ctx, int64_t t);
 /* Replace the observed values (not the coordinates) from HOST memory: the tensor's
  * values in the order given to s3_init and each coupled matrix's values likewise
  * (y_val may be NULL when n_coupled is 0; an entry y_val[m] may be NULL to keep that
- * matrix).  The host-to-device copy and the scatter into the library's layout are
- * enqueued on the stream; host buffers must stay valid until the stream reaches them. */
+ * matrix).  The host-to-device copy into one staging array is enqueued on the stream now;
+ * each of the library's layouts (minibatch, HOGWILD, BF16 HOGWILD, gradient and loss) gathers
+ * the staged values into its own order when a call next reads it, on the same stream.  Host
+ * buffers must stay valid until the stream reaches the copy. */
 int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val);
 
 /* The final QR step of Algorithm 1 (Section 3.4): for every mode n the thin QR

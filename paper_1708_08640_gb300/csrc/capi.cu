@@ -102,6 +102,10 @@ struct s3_ctx {
     float* grad_comp = nullptr;    // compensation buffers of the gradient (all parameters)
     int64_t grad_comp_n = 0;
     float* values_stage = nullptr; // s3_update_values staging (nnz + sum ynnz floats)
+    // per grouping (minibatch, HOGWILD, gradient, BF16 HOGWILD): whether its tensor values and
+    // each coupled matrix's values still wait to be gathered from values_stage
+    uint8_t stale_t[4] = {};
+    uint8_t stale_c[4][kMaxM] = {};
     int64_t ntest = 0;
     int32_t* test_idx[kMaxN] = {};
     float* test_val = nullptr;
@@ -772,9 +776,31 @@ extern "C" const char* s3_last_error(const s3_ctx* ctx) {
 }
 
 // ------------------------------------------------------------------ epoch
+// gathers the values staged by s3_update_values into grouping k's order (0 minibatch,
+// 1 HOGWILD, 2 gradient and loss, 3 BF16 HOGWILD) if they have not been yet
+static int refresh_values(s3_ctx* ctx, int k) {
+    DevGrouping* gs[4] = {&ctx->mb, &ctx->hog, &ctx->grad, &ctx->hog_bf};
+    DevGrouping* D = gs[k];
+    if (D->ngroups == 0) return S3_OK;   // not built for this context
+    if (ctx->stale_t[k]) {
+        KL(launch_gather_f32(D->tval, ctx->values_stage, D->t_src, D->t_off.back(), ctx->stream));
+        ctx->stale_t[k] = 0;
+    }
+    int64_t o = ctx->nnz;
+    for (int m = 0; m < ctx->M; ++m) {
+        if (ctx->stale_c[k][m]) {
+            KL(launch_gather_f32(D->cval[m], ctx->values_stage + o, D->c_src[m], ctx->ynnz[m], ctx->stream));
+            ctx->stale_c[k][m] = 0;
+        }
+        o += ctx->ynnz[m];
+    }
+    return S3_OK;
+}
+
 static int enqueue_minibatch(s3_ctx* ctx) {
     const int nF = ctx->N + ctx->M;
     if (ctx->mb_grid <= 0) return fail(ctx, S3_ERR_ARG, "the minibatch kernel cannot be made co-resident");
+    if (int rc = refresh_values(ctx, 0)) return rc;
     MbLaunch L{};
     for (int F = 0; F < nF; ++F) L.contrib[F] = ctx->contrib[F];
     L.core_part = ctx->core_part;
@@ -795,6 +821,7 @@ static int enqueue_minibatch(s3_ctx* ctx) {
 }
 
 static int enqueue_hogwild(s3_ctx* ctx) {
+    if (int rc = refresh_values(ctx, 1)) return rc;
     DevGrouping& D = ctx->hog;
     if (ctx->hog_smem > kMaxSmem)
         return fail(ctx, S3_ERR_ARG, "a HOGWILD tile needs " + std::to_string(ctx->hog_smem) +
@@ -825,6 +852,7 @@ static int enqueue_hogwild(s3_ctx* ctx) {
 }
 
 static int enqueue_hogwild_bf16(s3_ctx* ctx) {
+    if (int rc = refresh_values(ctx, 3)) return rc;
     DevGrouping& D = ctx->hog_bf;
     if (ctx->N != 3 || ctx->JP > 32)
         return fail(ctx, S3_ERR_ARG, "the BF16 form is built for 3-way tensors with ranks up to 32");
@@ -906,6 +934,7 @@ extern "C" int s3_loss(s3_ctx* ctx, double* f_out, double* rmse_out) {
     for (int m = 0; m < M; ++m) need = std::max<int64_t>(need, coupled_fwd_blocks(ctx->ynnz[m]));
     need = std::max<int64_t>(need, (int64_t)(nF + 1) * nb_sq);
     int rc;
+    if ((rc = refresh_values(ctx, 2)) != S3_OK) return rc;
     if ((rc = ensure_red(ctx, need * 2)) != S3_OK) return rc;
     float* parts_a = ctx->red_parts;
     // tensor squared errors over the train entries
@@ -1083,6 +1112,7 @@ extern "C" int s3_gradient(s3_ctx* ctx, const float* w, float* dG, float* const*
         CK(cudaMemsetAsync(outs[F], 0, (size_t)(factor_rows(ctx, F) * factor_cols(ctx, F)) * sizeof(float), ctx->stream));
     }
     DevGrouping& D = ctx->grad;
+    if (int rc = refresh_values(ctx, 2)) return rc;
     if (w) {
         // the caller's weights, from the order given to s3_init into the grouping's order
         if (!ctx->grad_w) CK(dalloc(ctx, &ctx->grad_w, (size_t)ctx->nnz));
@@ -1327,6 +1357,9 @@ extern "C" int s3_hog_config(s3_ctx* ctx, int precision, int64_t* ctas, int64_t*
 }
 
 // ------------------------------------------------------------------ values from the host
+// The values go to one staging array; each grouping gathers them into its own order only when
+// a call next reads that grouping (refresh_values), so an epoch after an update pays for the
+// one layout it uses, not for all four.
 extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* const* y_val) {
     if (!usable(ctx)) return S3_ERR_STATE;
     if (!x_val) return fail(ctx, S3_ERR_ARG, "x_val is NULL");
@@ -1334,20 +1367,13 @@ extern "C" int s3_update_values(s3_ctx* ctx, const float* x_val, const float* co
     for (int m = 0; m < ctx->M; ++m) total += ctx->ynnz[m];
     if (!ctx->values_stage) CK(dalloc(ctx, &ctx->values_stage, (size_t)total));
     CK(cudaMemcpyAsync(ctx->values_stage, x_val, (size_t)ctx->nnz * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    DevGrouping* gs[4] = {&ctx->mb, &ctx->hog, &ctx->grad, &ctx->hog_bf};
-    // groupings that were not built for this context (ngroups 0) hold no arrays
-    for (DevGrouping* D : gs)
-        if (D->ngroups > 0)
-            KL(launch_gather_f32(D->tval, ctx->values_stage, D->t_src, D->t_off.back(), ctx->stream));
+    for (int k = 0; k < 4; ++k) ctx->stale_t[k] = 1;
     int64_t o = ctx->nnz;
     for (int m = 0; m < ctx->M; ++m) {
         if (y_val && y_val[m]) {
             CK(cudaMemcpyAsync(ctx->values_stage + o, y_val[m], (size_t)ctx->ynnz[m] * sizeof(float),
                                cudaMemcpyHostToDevice, ctx->stream));
-            for (DevGrouping* D : gs)
-                if (D->ngroups > 0)
-                    KL(launch_gather_f32(D->cval[m], ctx->values_stage + o, D->c_src[m], ctx->ynnz[m],
-                                         ctx->stream));
+            for (int k = 0; k < 4; ++k) ctx->stale_c[k][m] = 1;
         }
         o += ctx->ynnz[m];
     }

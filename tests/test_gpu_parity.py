@@ -220,6 +220,54 @@ def test_update_values(cuda_lib, problems):
     assert rel(gpu.loss()[0], o2.loss()[0]) <= 1e-5
 
 
+def test_update_values_reach_every_layout(cuda_lib, problems):
+    """s3_update_values stages the values once; each layout takes them when a call next reads
+    it.  After two updates (the second without coupled values, which keep the first's): the
+    loss and the gradient equal the oracle's on those values (1e-5), a minibatch epoch its
+    epoch (1e-4, the multi-epoch bound), and a HOGWILD epoch on one CTA the epoch of a
+    context built with them (1e-5)."""
+    from paper_1708_08640_gb300.model import S3CMTF
+    p = problems["cfg0"]
+    gpu, _, q, order = make_pair(p, batch=256)
+    rng = np.random.default_rng(10)
+    y1 = f32(rng.normal(size=q.coupled[0].nnz))
+    x2 = f32(rng.normal(size=q.nnz) + 2.0)
+    gpu.update_values(f32(rng.normal(size=q.nnz)).astype(np.float32), [y1.astype(np.float32)])
+    gpu.update_values(x2.astype(np.float32))
+    q2 = fp32_problem(p)
+    q2.train_val = x2
+    q2.coupled[0].vals = y1
+    params = fp32_params(synth.init_params(p, 1))
+    hp = {k: v for k, v in p.hparams.items() if k in ("lr0", "mu", "lambda_reg", "lambda_m", "core_scale")}
+    o2 = oracle.Oracle(q2, batch=256, **hp)
+    o2.set_params(*params)
+    assert rel(gpu.loss()[0], o2.loss()[0]) <= 1e-5
+    dG, dU, dV = gpu.gradient()
+    gG, gU, gV = o2.full_gradient()
+    assert rel(as_np(dG), gG) <= 1e-5
+    assert all(rel(as_np(a), b) <= 1e-5 for a, b in zip(dU, gU))
+    gpu.epoch("minibatch")
+    o2.epoch_minibatch(0, order)
+    G, U, _ = gpu.get_params()
+    assert rel(as_np(G), o2.G) <= 1e-4
+    assert all(rel(as_np(a), b) <= 1e-4 for a, b in zip(U, o2.U))
+    # HOGWILD on one CTA: this context (values updated) against one built with them
+    h = dict(p.hparams, hog_ctas=1)
+    a = S3CMTF.from_problem(q, order=order, **h)
+    b = S3CMTF.from_problem(q2, order=order, **h)
+    for m in (a, b):
+        m.set_params(*params)
+    a.update_values(x2.astype(np.float32), [y1.astype(np.float32)])
+    a.epoch("hogwild")
+    b.epoch("hogwild")
+    Ga, Ua, _ = a.get_params()
+    Gb, Ub, _ = b.get_params()
+    assert rel(as_np(Ga), as_np(Gb)) <= 1e-5
+    assert all(rel(as_np(x), as_np(y)) <= 1e-5 for x, y in zip(Ua, Ub))
+    for m in (gpu, a, b):
+        m.close()
+
+
 def test_no_coupled_small_rank_and_ragged(cuda_lib):
     """J = 1 and J = 3 (padded ranks), no coupled matrix, nnz not a multiple of 256, rows
     without entries."""
