@@ -199,6 +199,47 @@ __device__ __forceinline__ void load_core_bf16(const DParams& P, uint8_t* smem_r
     }
 }
 
+// The tile's row steps (hog_flush) with the rows' quad count fixed at compile time when the
+// context's rows are as wide as the slots (ranks 16, 20, 32): an item's (segment, quad) split
+// is then a shift or a multiply instead of a division by a runtime value, and the step's
+// division by the event count is taken only under the MEAN rule.  The same sums, steps and
+// order as hog_flush; at rank 32 each SM sub-partition runs one entry warp, so every
+// instruction of this loop is on the tile's critical path.
+template <int JPR>
+__device__ __forceinline__ void flush_rows_bf16(const DParams& P, const float* smem, const HogSmem& H,
+                                                float eta, int row_mean, int first, int stride) {
+    if (P.ld != JPR) {
+        hog_flush<JPR>(P, smem, H, eta, row_mean, first, stride);
+        return;
+    }
+    constexpr int SS = slot_stride(JPR), NQ = JPR / 4;
+    const int* cnts = reinterpret_cast<const int*>(smem + H.noff);
+    for (int F = 0; F < H.nF; ++F) {
+        const int nseg = cnts[F];
+        const float* sa = smem + H.off[F];
+        const int4* tab = reinterpret_cast<const int4*>(smem + H.toff[F]);
+        float* base = F < P.N ? P.U[F] : P.V[F - P.N];
+        for (int l = first; l < nseg * NQ; l += stride) {
+            const int s = l / NQ, q = l % NQ;
+            const int4 sg = tab[s];   // row, first slot, events, step scale
+            const int32_t rr = sg.x, st = sg.y, cnt = sg.z;
+            float4 acc = *reinterpret_cast<const float4*>(sa + st * SS + 4 * q);
+            for (int k = 1; k < cnt; ++k) {
+                const float4 v = *reinterpret_cast<const float4*>(sa + (st + k) * SS + 4 * q);
+                acc.x += v.x;
+                acc.y += v.y;
+                acc.z += v.z;
+                acc.w += v.w;
+            }
+            float sc = -eta * __int_as_float(sg.w);
+            if (row_mean) sc /= (float)cnt;
+            float* dst = base + (int64_t)rr * JPR + 4 * q;
+            red_add_v4(dst, sc * acc.x, sc * acc.y, sc * acc.z, sc * acc.w);
+            if (P.nonneg) red_proj_v4(dst);
+        }
+    }
+}
+
 template <int JQ, int JK>
 __global__ void __launch_bounds__(kBfThreads, BfLayout<JQ, JK>::CTAS_PER_SM)
 k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, const float* eta_p,
@@ -550,7 +591,7 @@ k_tensor_hog_bf16(DParams P, DGroup Gr, int64_t n_tiles, int* tile_counter, cons
             const bool failed = s_stop != 0;
             int64_t lo = 0, hi = 0;
             if (tid < 32) hog_ranges(P, Gr, s_nxt, n_tiles, H, tid, lo, hi);
-            if (!failed) hog_flush<JPR>(P, smem, H, eta, row_mean, tid, kBfTile);
+            if (!failed) flush_rows_bf16<JPR>(P, smem, H, eta, row_mean, tid, kBfTile);
             since_sync += 1;
             acc_tiles += nb > 0;
             // ---- the core step of the tiles since the last one, when due (and always at the
