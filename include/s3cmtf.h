@@ -104,10 +104,9 @@ typedef struct {
                            have kappa > gamma updates in flight at once (kappa = its
                            occurrences x entries in flight / |Omega|) takes its step scaled by
                            gamma / kappa; every other row takes the plain lock-free step.
-                           0 = default 360 / J up to a largest rank J of 16, i.e. 36 at rank
-                           10 (a coupled entry's step grows stiffer with the rank), and
-                           (360 / J) sqrt(16 / J) above (7.95 at 32); 2000 / J in the
-                           non-negative form; < 0 disables the scaling. */
+                           0 = default 360 / (largest rank), i.e. 36 at rank 10 (a coupled
+                           entry's step grows stiffer with the rank), and 2000 / (largest rank)
+                           in the non-negative form; < 0 disables the scaling. */
     int hog_ctas;       /* HOGWILD: CTAs working at once (0 = default: on 3-way tensors, enough
                            for a budget of tensor entries in flight -- 29184 up to rank 10,
                            29184 (10 / J)^0.6 at a larger largest rank J, three quarters of that

@@ -673,11 +673,7 @@ extern "C" int s3_init(s3_ctx** out, const s3_coo_tensor* train, const s3_coo_ma
         // as the plain group steps do, so that the plain form's stronger damping of hot rows
         // leaves it 2-3% above projected Algorithm 1, while this setting keeps it within 1%
         // (cfg1, rank 10: 0.82%).
-        // Above rank 16 the plain form takes (360 / J) sqrt(16 / J), 7.95 at rank 32: there
-        // 360 / J = 11.25 left the first epoch 1.0% below Algorithm 1 (cfg1), 8 leaves it
-        // 0.4% (FP32) and 0.3% (BF16) below, 6 0.3% above and 4 1.3% above.
         double gamma = (hp->nonneg ? 2000.0 : 360.0) / jmax;
-        if (!hp->nonneg && jmax > 16) gamma *= std::sqrt(16.0 / jmax);
         if (hp->hog_staleness != 0.f) gamma = (double)hp->hog_staleness;
         auto row_scales = [&](DevGrouping& D, double inflight) -> int {
             for (int F = 0; F < nF; ++F) {
